@@ -1,0 +1,268 @@
+/*
+ * dpde.h -- C ABI of the GB300 DPDE timestep library (libdpde.so).
+ *
+ * Method: Dissipative Particle Dynamics with Energy conservation (DPDE) as
+ * defined by Homman, Maillet, Roussel and Stoltz, "New parallelizable schemes
+ * for integrating the Dissipative Particle Dynamics with Energy Conservation"
+ * (arXiv:1507.06643). Section II.A, Eq. (DPDE), gives the dynamics of a
+ * particle's position q_i, momentum p_i and internal energy eps_i; friction and
+ * noise act on the full relative velocity (not projected on the line of
+ * centres). Section III splits one timestep into a velocity-Verlet step of the
+ * Hamiltonian part (Eq. newton) followed by a fluctuation/dissipation (FD) step
+ * (Eq. DPDE_dissipative) integrated by one of the schemes of Sec. III.A/III.B.
+ *
+ * Everything below is plain C: pointers, sizes and status codes. The library
+ * owns every device buffer it allocates; caller arrays are only read or
+ * written during the call that receives them.
+ *
+ * ---------------------------------------------------------------------------
+ * Units, model and conventions (reduced units, k_B = 1, dimension d = 3)
+ * ---------------------------------------------------------------------------
+ *  - Cut-off function, Eq. (pot_mou): chi(r) = (1 - r/r_cut)^2 for r < r_cut,
+ *    else 0; the noise amplitude uses sqrt(chi) = 1 - r/r_cut. A pair
+ *    interacts iff r^2 < r_cut^2 (chi, its root and the force all vanish at
+ *    r_cut, so the strict inequality only matters to rounding).
+ *  - Conservative potential: soft repulsion v(r) = (a r_cut / 2)(1 - r/r_cut)^2
+ *    for r < r_cut, force on i from j: a (1 - r/r_cut) (q_i - q_j)/r; a pair at
+ *    r = 0 exerts no force. U = sum over pairs i<j of v(r_ij) (Eq.
+ *    def_potential_energy with this v).
+ *  - Equation of state, Eq. (DPDE_internalEOS) with constant heat capacity:
+ *    eps_i = C_v T_i, so beta_i = 1/T_i = C_v / eps_i.
+ *  - Fluctuation/dissipation relation, Eq. (DPDE_fd):
+ *    gamma_ij = (sigma^2 / 4) (beta_i + beta_j).
+ *  - Total energy (Sec. II.A): E = U + sum_i |p_i|^2 / (2 m) + sum_i eps_i.
+ *    The paper prints the kinetic term without the 1/2; the kinetic energy
+ *    variations of Eqs. (SSA_ij) and (SER_eint_discretization) fix it as
+ *    |p|^2/(2m), which is what is conserved here.
+ *  - Periodic boxes [0, L_x) x [0, L_y) x [0, L_z), minimum-image distances.
+ *
+ * ---------------------------------------------------------------------------
+ * Particle identity and noise (Sec. III.A, the remark under Eq. SEM_fd; Sec.
+ * III.B.1, the closing paragraph on regenerating G_ij^n)
+ * ---------------------------------------------------------------------------
+ *  - Particles of replica r are identified by id = 0 .. n_r-1, their index in
+ *    the arrays handed to dpde_set_state (within that replica's segment).
+ *  - The Gaussian increment of pair (i, j) at step n is a pure function of
+ *    (seed, n, replica, min id, max id):
+ *       x[0..3] = Philox4x32-10(counter = {id_min, id_max, (uint32)n, replica},
+ *                               key     = {seed & 0xffffffff, seed >> 32})
+ *    (Salmon, Moraes, Dror, Shaw, SC'11: multipliers 0xD2511F53, 0xCD9E8D57,
+ *    Weyl key increments 0x9E3779B9, 0xBB67AE85, ten rounds).
+ *    Uniforms with 24 significant bits, exact in float and double:
+ *       u1 = ((x[0] >> 8) + 1) * 2^-24   in (0, 1]
+ *       t1 = ( x[1] >> 8)      * 2^-24   in [0, 1)
+ *       u2 = ((x[2] >> 8) + 1) * 2^-24,  t2 = (x[3] >> 8) * 2^-24
+ *    Box-Muller: R_k = sqrt(-2 ln u_k);
+ *       G = ( R1 cos(2 pi t1), R1 sin(2 pi t1), R2 cos(2 pi t2) ).
+ *    G is G_ij for the ordered pair (id_min, id_max); G_ji = -G_ij. Tails are
+ *    capped at |G_k| <= sqrt(48 ln 2) ~ 5.77.
+ *
+ * ---------------------------------------------------------------------------
+ * One timestep (dpde_step), from state (q^n, p^n, eps^n) and F^n = F(q^n)
+ * ---------------------------------------------------------------------------
+ *  1. Velocity-Verlet (Sec. III.A, "standard Velocity-Verlet"):
+ *       p <- p + (dt/2) F^n ;  q <- wrap(q + dt p / m)
+ *       F^{n+1} = F(q^{n+1}) ;  p <- p + (dt/2) F^{n+1}
+ *     wrap: x >= L -> x - L ; x < 0 -> x + L (one correction per step).
+ *  2. Fluctuation/dissipation on the post-Verlet state with noise G^n
+ *     (Trotter splitting, Appendix B.1: Hamiltonian part first):
+ *       DPDE_SER    Eq. (SER_p) then Eq. (SER_eint_discretization): both sweeps
+ *                   use the same pre-FD p and eps; updates are applied after
+ *                   the second sweep. The energy update uses the factor -1/2
+ *                   of Eq. (SER_eint_discretization) (Eq. SER_fd drops it; only
+ *                   the -1/2 form conserves energy exactly).
+ *       DPDE_HYBRID Sec. III.B.2: the SSA pair map of Eq. (SSA_ij) applied in
+ *                   sequence to every interacting pair whose two particles lie
+ *                   in the same domain ("processor"), in the order defined
+ *                   below, then SER over all remaining (cross-domain) pairs on
+ *                   the post-SSA state.
+ *       DPDE_SEM    Eq. (SEM_fd) (Euler-Maruyama; does not conserve energy).
+ *       DPDE_SSA    Eq. (SSA_ij) over all interacting pairs (Hybrid with one
+ *                   domain spanning the periodic replica).
+ *     The SSA map uses a = +2 gamma_ij chi dt / m (the printed minus sign is a
+ *     typo: the map is the exact Ornstein-Uhlenbeck transition of
+ *     p_ij = p_i - p_j at fixed gamma_ij, whose decay rate is 2 gamma chi / m);
+ *     gamma_ij is evaluated from the current eps_i, eps_j of the sequence.
+ *  3. n <- n + 1.
+ *
+ * ---------------------------------------------------------------------------
+ * Cell grid, domains ("bricks") and the SSA order
+ * ---------------------------------------------------------------------------
+ *  For a replica with box L and brick grid B = (B_x, B_y, B_z):
+ *       k_d     = floor(L_d / (B_d r_cut))   cells per brick along d (>= 1)
+ *       ncell_d = B_d k_d                     (must be >= 3)
+ *       c_d(x)  = min(ncell_d - 1, (int)(x * (ncell_d / L_d)))
+ *       brick_d = c_d / k_d
+ *  The quotient ncell_d / L_d is formed once in double. A pair is "intra
+ *  domain" (set A of Sec. III.B.2) iff both particles have the same brick.
+ *  Order of the SSA sequence over A (the paper leaves it free, Sec. III.A.2):
+ *   rounds over the 14 half-stencil directions delta in this order
+ *     (0,0,0), (1,0,0), (-1,1,0), (0,1,0), (1,1,0), (-1,-1,1), (0,-1,1),
+ *     (1,-1,1), (-1,0,1), (0,0,1), (1,0,1), (-1,1,1), (0,1,1), (1,1,1)
+ *   (delta = (dx, dy, dz)); the leading axis of delta is z if dz != 0, else y
+ *   if dy != 0, else x. Within direction delta, colours col = 0, 1, (2):
+ *   col(c) = (local coordinate of c along the leading axis) mod 2, except
+ *   that when the brick is periodic along that axis (B = 1) and k is odd the
+ *   last local cell takes colour 2. Within (delta, col) the cell pairs
+ *   (c, c + delta) (both in the same brick; the neighbour wraps only along
+ *   periodic-brick axes) are disjoint and may be processed in any order. Within
+ *   one cell pair, particles i of c (ascending id) outer, j of c + delta
+ *   (ascending id) inner; for delta = 0, pairs i < j of c in that order.
+ *
+ * ---------------------------------------------------------------------------
+ * Precision modes
+ * ---------------------------------------------------------------------------
+ *  DPDE_FP64  : every quantity in double.
+ *  DPDE_MIXED : q, p, forces and pair arithmetic in float; eps in double. The
+ *               internal-energy updates account in double for the kinetic
+ *               energy change of the stored float momenta, so the FD part
+ *               conserves the double-evaluated total energy to rounding of
+ *               the per-particle antisymmetric pair sums (equal in exact
+ *               arithmetic to Eq. SER_eint_discretization and Eq. SSA_ij).
+ */
+#ifndef DPDE_H
+#define DPDE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes (every entry point returns one) ---- */
+#define DPDE_OK                 0
+#define DPDE_ERR_ARG           -1  /* invalid argument; nothing was changed   */
+#define DPDE_ERR_CUDA          -2  /* CUDA runtime error (message kept)       */
+#define DPDE_ERR_OOM           -3  /* device allocation failed                */
+#define DPDE_ERR_NEG_EPS       -4  /* some eps_i <= 0 after the last step(s);
+                                      the state was advanced, nothing clamped */
+#define DPDE_ERR_NONFINITE     -5  /* NaN/Inf in the state                    */
+#define DPDE_ERR_TIMEOUT       -6  /* a bounded device wait gave up           */
+
+/* ---- enumerations ---- */
+#define DPDE_FP64   0
+#define DPDE_MIXED  1
+
+#define DPDE_SER     0
+#define DPDE_HYBRID  1
+#define DPDE_SEM     2
+#define DPDE_SSA     3
+
+/* Global model parameters (shared by all replicas of a handle). */
+typedef struct dpde_params {
+    double   mass;       /* m  > 0                                          */
+    double   r_cut;      /* r_cut > 0: range of chi and of the soft force   */
+    double   a;          /* soft-repulsion amplitude a >= 0                 */
+    double   sigma;      /* fluctuation strength sigma >= 0, Eq. (DPDE_fd)  */
+    uint64_t seed;       /* Philox key                                      */
+    int32_t  precision;  /* DPDE_FP64 or DPDE_MIXED                         */
+    int32_t  reserved;   /* must be 0                                       */
+} dpde_params;
+
+/* One independent system ("replica", one of the N_traj trajectories of
+ * Eq. obs_time_estimation_traj). */
+typedef struct dpde_replica {
+    int64_t n;           /* number of particles, >= 0                       */
+    double  box[3];      /* L_x, L_y, L_z > 0                               */
+    double  cv;          /* constant heat capacity C_v > 0                  */
+    int32_t bricks[3];   /* Hybrid domain grid B_d >= 1 (1,1,1 = one domain) */
+    int32_t reserved;    /* must be 0                                       */
+} dpde_replica;
+
+/* Observables of one replica at the current state (Sec. II.B). */
+typedef struct dpde_obs {
+    double  E;           /* U + K + Eint                                    */
+    double  K;           /* sum |p|^2 / (2m)                                */
+    double  U;           /* potential energy                                */
+    double  Eint;        /* sum eps_i                                       */
+    double  P[3];        /* total momentum                                  */
+    double  Tkin;        /* 2K / (d (n-1)), Eq. (Tkin), instantaneous       */
+    double  Tint;        /* n / sum(C_v/eps_i), Eq. (Tint), instantaneous   */
+    double  Tpot_num;    /* |grad U|^2 = sum |F_i|^2 (numerator of Eq. Tcon) */
+    double  Tpot_den;    /* Laplacian of U (denominator of Eq. Tcon)        */
+    int64_t step;        /* steps taken since dpde_set_state                */
+    int64_t n;           /* particles in the replica                        */
+    int64_t neg_eps;     /* number of eps_i <= 0                            */
+    int64_t nonfinite;   /* number of particles with a NaN/Inf component    */
+} dpde_obs;
+
+typedef struct dpde_handle dpde_handle;
+
+/* Creates a handle on the current CUDA device.
+ *  params      : model parameters (copied).
+ *  n_replicas  : >= 1.
+ *  replicas    : n_replicas descriptors (copied). Every replica needs
+ *                ncell_d = B_d floor(L_d/(B_d r_cut)) >= 3 and k_d >= 1.
+ *  stream      : cudaStream_t to run on (NULL = legacy default stream). The
+ *                caller keeps it alive for the handle's lifetime.
+ *  out         : receives the handle (NULL on failure).
+ * Allocates all device buffers for sum_r n_r particles. Errors: DPDE_ERR_ARG,
+ * DPDE_ERR_OOM, DPDE_ERR_CUDA. */
+int dpde_create(const dpde_params* params, int32_t n_replicas,
+                const dpde_replica* replicas, void* stream, dpde_handle** out);
+
+/* Sets the state of every replica and resets the step counter to `step`.
+ *  q, p     : 3*N doubles, particle-major (x,y,z), replicas concatenated in
+ *             order, ids = index within the replica's segment. q is wrapped
+ *             into the box. In DPDE_MIXED mode q, p are rounded to float.
+ *  eps      : N doubles.
+ *  on_device: 0 = host pointers, 1 = device pointers (e.g. torch data_ptr()).
+ * Computes the forces F(q) of the new state. Synchronous. */
+int dpde_set_state(dpde_handle* h, const double* q, const double* p,
+                   const double* eps, int64_t step, int32_t on_device);
+
+/* Copies the state out in id order (same layout as dpde_set_state); q in
+ * [0, L). Any of q, p, eps may be NULL. Synchronous; returns the device
+ * status (DPDE_ERR_NEG_EPS / DPDE_ERR_NONFINITE) raised since the last check. */
+int dpde_get_state(dpde_handle* h, double* q, double* p, double* eps,
+                   int32_t on_device);
+
+/* Advances every replica by n >= 0 steps of size dt > 0 with the given scheme
+ * (DPDE_SER, DPDE_HYBRID, DPDE_SEM, DPDE_SSA). Asynchronous on the handle's
+ * stream; the returned status covers argument and launch errors. Device-side
+ * conditions surface at the next dpde_sync / dpde_get_state /
+ * dpde_observables. The step sequence is replayed from a captured CUDA graph
+ * when use_graph != 0 (captured on first use per (dt, scheme)). */
+int dpde_step(dpde_handle* h, int64_t n, double dt, int32_t scheme,
+              int32_t use_graph);
+
+/* Waits for the stream and returns the device status raised since the last
+ * check (DPDE_OK, DPDE_ERR_NEG_EPS, DPDE_ERR_NONFINITE). */
+int dpde_sync(dpde_handle* h);
+
+/* Computes the observables of every replica into out[0 .. n_replicas-1].
+ * Synchronous. Returns DPDE_ERR_NEG_EPS / _NONFINITE when the state holds
+ * such values (out is still filled). */
+int dpde_observables(dpde_handle* h, dpde_obs* out);
+
+/* Current step counter (steps since dpde_set_state plus its `step`). */
+int dpde_get_step(dpde_handle* h, int64_t* step);
+
+/* Frees the handle (NULL is accepted). */
+int dpde_destroy(dpde_handle* h);
+
+/* Last error message of the handle (or of the last failed dpde_create when h
+ * is NULL). Never NULL; valid until the next call on the same handle. */
+const char* dpde_last_error(const dpde_handle* h);
+
+/* ---- diagnostics ---- */
+
+/* Runs the device Philox4x32-10 of the library on n (counter, key) pairs:
+ * ctr is 4n uint32, key 2n uint32, out 4n uint32, all host pointers.
+ * Used to check the device generator bit for bit. Synchronous. */
+int dpde_debug_philox(int64_t n, const uint32_t* ctr, const uint32_t* key,
+                      uint32_t* out);
+
+/* Returns the library's device Gaussian triple G for n pairs
+ * (seed, step, replica, id_a, id_b), with the sign convention G_ab = -G_ba:
+ * out is 3n doubles (computed in double when precision = DPDE_FP64, in float
+ * otherwise). Host pointers. Synchronous. */
+int dpde_debug_gaussian(int64_t n, uint64_t seed, const uint32_t* step,
+                        const uint32_t* replica, const uint32_t* id_a,
+                        const uint32_t* id_b, int32_t precision, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPDE_H */

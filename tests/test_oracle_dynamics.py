@@ -1,0 +1,117 @@
+"""Pins of the oracle's full timestep: velocity Verlet (Sec. III.A) and the
+equilibrium the fluctuation/dissipation relation fixes (Sec. II.B).
+
+- With sigma = 0 the FD part is the identity and the step is plain velocity
+  Verlet: energy error O(dt^2), exact time reversibility, exact momentum.
+- Equilibrium: T_kin = T_int at equilibrium (Eq. Tkin, Eq. Tint and the
+  remark that all temperature estimators agree).
+- A run split in two pieces equals the same run done at once (the noise is a
+  pure function of (seed, step, ids)).
+"""
+import math
+
+import numpy as np
+import pytest
+
+
+def state(n, box, seed, cv=100.0, kT=1.0):
+    rng = np.random.default_rng(seed)
+    q = rng.random((n, 3)) * np.asarray(box)
+    p = rng.standard_normal((n, 3)) * math.sqrt(kT)
+    p -= p.mean(axis=0)
+    eps = cv * kT * (1 + 0.05 * rng.uniform(-1, 1, n))
+    return q, p, eps
+
+
+def min_image(d, box):
+    box = np.asarray(box)
+    return d - box * np.round(d / box)
+
+
+def test_verlet_energy_error_is_second_order(ora):
+    n, box = 200, (4.05,) * 3
+    q, p, eps = state(n, box, seed=31)
+    rep = ora.make_replica(n, box, 100.0)
+    prm = ora.make_params(sigma=0.0)
+    # relax overlaps first so that the energy error is in the asymptotic regime
+    S = ora.System([rep], prm, q, p, eps)
+    S.run(200, 0.002, "SER")
+    q0, p0, e0 = S.q.copy(), S.p.copy(), S.eps.copy()
+    errs = []
+    for dt in (0.01, 0.005):
+        S = ora.System([rep], prm, q0, p0, e0)
+        E0 = S.observables()["E"]
+        worst = 0.0
+        for _ in range(int(round(0.5 / dt))):
+            S.run(1, dt, "SER")
+            worst = max(worst, abs(S.observables()["E"] - E0))
+        errs.append(worst)
+        assert np.array_equal(S.eps, e0)          # sigma = 0: FD is the identity
+    ratio = errs[0] / errs[1]
+    assert 3.0 < ratio < 5.0, ratio
+
+
+def test_verlet_time_reversible_and_momentum(ora):
+    n, box = 200, (4.05,) * 3
+    q, p, eps = state(n, box, seed=32)
+    rep = ora.make_replica(n, box, 100.0)
+    prm = ora.make_params(sigma=0.0)
+    S = ora.System([rep], prm, q, p, eps)
+    P0 = S.p.sum(axis=0)
+    S.run(100, 0.005, "SER")
+    assert np.max(np.abs(S.p.sum(axis=0) - P0)) < 1e-11
+    S.p = -S.p
+    S.run(100, 0.005, "SER")
+    assert np.max(np.abs(min_image(S.q - q, box))) < 1e-9
+    assert np.max(np.abs(S.p + p)) < 1e-9
+
+
+@pytest.mark.parametrize("scheme", ["SER", "HYBRID", "SSA", "SEM"])
+def test_split_run_equals_single_run(ora, scheme):
+    n, box = 300, (4.64,) * 3
+    q, p, eps = state(n, box, seed=33)
+    rep = ora.make_replica(n, box, 100.0, (1, 1, 1) if scheme != "HYBRID" else (1, 2, 1))
+    prm = ora.make_params(seed=77)
+    A = ora.System([rep], prm, q, p, eps)
+    A.run(10, 0.01, scheme)
+    B = ora.System([rep], prm, q, p, eps)
+    B.run(4, 0.01, scheme)
+    C = ora.System([rep], prm, B.q, B.p, B.eps, step=B.step)
+    C.run(6, 0.01, scheme)
+    assert np.array_equal(A.q, C.q) and np.array_equal(A.p, C.p) and np.array_equal(A.eps, C.eps)
+
+
+def test_replicas_are_independent(ora):
+    box = (4.64,) * 3
+    q1, p1, e1 = state(300, box, seed=34)
+    q2, p2, e2 = state(200, (4.2,) * 3, seed=35, cv=10.0)
+    r1 = ora.make_replica(300, box, 100.0)
+    r2 = ora.make_replica(200, (4.2,) * 3, 10.0)
+    prm = ora.make_params(seed=5)
+    both = ora.System([r1, r2], prm, np.vstack([q1, q2]), np.vstack([p1, p2]), np.concatenate([e1, e2]))
+    both.run(5, 0.01, "SER")
+    alone = ora.System([r1], prm, q1, p1, e1)
+    alone.run(5, 0.01, "SER")
+    assert np.array_equal(both.p[:300], alone.p) and np.array_equal(both.eps[:300], alone.eps)
+    # replica index enters the noise: replica 1 alone (index 0) differs
+    alone2 = ora.System([r2], prm, q2, p2, e2)
+    alone2.run(5, 0.01, "SER")
+    assert not np.array_equal(both.p[300:], alone2.p)
+
+
+@pytest.mark.parametrize("scheme,dt,tol", [("SSA", 0.01, 0.04), ("HYBRID", 0.01, 0.04),
+                                           ("SER", 0.005, 0.05)])
+def test_equilibrium_kinetic_equals_internal_temperature(ora, scheme, dt, tol):
+    n, box = 300, (4.64,) * 3
+    q, p, eps = state(n, box, seed=36, cv=10.0)
+    rep = ora.make_replica(n, box, 10.0, (2, 1, 1))
+    S = ora.System([rep], ora.make_params(sigma=3.0, seed=3), q, p, eps)
+    S.run(int(5.0 / dt), dt, scheme)              # relax
+    tk, ti = [], []
+    for _ in range(200):
+        S.run(int(0.1 / dt), dt, scheme)
+        o = S.observables()
+        tk.append(o["Tkin"])
+        ti.append(o["Tint"])
+    tk, ti = np.mean(tk), np.mean(ti)
+    assert abs(tk / ti - 1) < tol, (tk, ti)
