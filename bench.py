@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the DPDE timestep (particle-steps/s).
+
+One "step" is one full DPDE timestep of the workload: velocity Verlet with the
+cell-list rebuild, conservative forces, and the fluctuation/dissipation scheme
+(default: Hybrid, which runs the SSA rounds over intra-domain pairs and the two
+SER sweeps over cross-domain pairs). Default workload: 4,000,000 particles at
+density 3 (L ~ 110.1), C_v = 50, mixed precision (float q/p/F, double eps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sub-box sample of the
+same workload (same density and parameters). Under torchrun every rank runs
+its own independent replica of the workload (weak scaling); rank 0 prints one
+JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s at N=4M on 1 GB300 (mixed vs FP64) at stated energy drift"
+UNIT = "particle-steps/s"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.dev)], stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return None
+        try:
+            sm = [float(r[1]) for r in rows]
+            smax = max(float(r[2]) for r in rows)
+        except ValueError:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = [x for x in sm if x > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def workload_and_scheme(args):
+    from paper_1507_06643_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload](args.precision)
+    return w
+
+
+def algorithmic_model(w, phase: str, phases_ms: dict, precision: str):
+    """Algorithmic work of one launch of the dominant phase (see the design doc,
+    'Roofline'): unique pairs x operations per pair for the FD sweeps and the
+    SSA pass (ALU-bound), bytes for the memory-bound sort/force phases."""
+    n = w.n_total
+    pairs_unique = n * 2.0 * math.pi * 3.0 / 3.0  # (4/3 pi rho r_c^3)/2 per particle
+    state_bytes = 16 if precision == "mixed" else 32
+    if phase in ("sweep1", "sweep2", "ssa"):
+        ops = {"sweep1": 170.0, "sweep2": 185.0, "ssa": 230.0}[phase]
+        return "alu", pairs_unique * ops, "Gop/s"
+    if phase == "force":
+        return "hbm", n * (state_bytes * 4.0), "GB/s"
+    return "hbm", n * (state_bytes * 4.0 + 8 * 2 + 12), "GB/s"
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as tdist
+    from paper_1507_06643_gb300 import dpde, inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = workload_and_scheme(args)
+    spec_reps = [dpde.make_replica(s.n, s.box, s.cv, s.bricks) for s in w.replicas]
+    prm = dpde.make_params(w.mass, w.r_cut, w.a, w.sigma, w.seed + 7919 * rank, w.precision)
+    q, p, e = inputs.workload_state(w, seed=w.seed + rank)
+    stream = torch.cuda.Stream()
+    S = dpde.System(prm, spec_reps, stream=stream.cuda_stream)
+    S.set_state(q, p, e)
+    obs0 = S.observables()
+    dt = w.dt
+
+    S.step(args.warmup, dt, args.scheme)
+    assert S.sync() == dpde.DPDE_OK
+    if world > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t0.record(stream)
+        S.step(args.steps, dt, args.scheme)
+        t1.record(stream)
+        t1.synchronize()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    status = S.sync()
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        tdist.all_reduce(ms_t, op=tdist.ReduceOp.MAX)
+        tdist.barrier()
+    ms = float(ms_t.item())
+    obs1 = S.observables()
+    n_tot = w.n_total
+    value = n_tot * world * args.steps / (ms / 1e3)
+
+    # per-phase kernel times (CUDA events on the launching stream, eager launches)
+    phases = S.step_profiled(args.profile_steps, dt, args.scheme)
+    phase_avg = {k: v / args.profile_steps for k, v in phases.items()}
+    dom = max(phase_avg, key=phase_avg.get)
+
+    # end to end through the C ABI with pinned host buffers
+    qh = torch.from_numpy(q).pin_memory()
+    ph = torch.from_numpy(p).pin_memory()
+    eh = torch.from_numpy(e).pin_memory()
+    S2 = dpde.System(prm, spec_reps, stream=stream.cuda_stream)
+    e2e_steps = args.e2e_steps
+    S2.set_state(qh, ph, eh)
+    torch.cuda.synchronize()
+    tt = time.perf_counter()
+    for _ in range(e2e_steps):
+        dpde.dpde_set_state(S2.h, qh, ph, eh, 0, False)
+        S2.step(1, dt, args.scheme)
+        rc = dpde.dpde_get_state(S2.h, qh, ph, eh, False)
+        assert rc == dpde.DPDE_OK
+    e2e_s = time.perf_counter() - tt
+    S2.close()
+    e2e = {"value": n_tot * world * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(q.nbytes + p.nbytes + e.nbytes),
+           "d2h_bytes_per_step": int(q.nbytes + p.nbytes + e.nbytes)}
+
+    peaks, peak_src = measured_peaks()
+    bound, work, unit = algorithmic_model(w, dom, phase_avg, w.precision)
+    dom_s = phase_avg[dom] / 1e3
+    achieved = work / dom_s / 1e9
+    if bound == "alu":
+        clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = 152 * 128 * clk_mhz * 1e6 / 1e9   # FP32/INT32 lane-ops per second (G)
+        peak_note = f"152 SMs x 128 FP32/INT32 lanes x {clk_mhz:.0f} MHz ({peak_src} clock)"
+    else:
+        peak = float(peaks["hbm_gbs"])
+        peak_note = f"{peak_src} hbm_gbs"
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_note}
+
+    drift = abs(obs1[0]["E"] - obs0[0]["E"]) / abs(obs0[0]["E"])
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if w.precision == "mixed" else "f64",
+        "data": "synthetic: uniform positions, Maxwellian momenta (kT=1), eps = C_v kT (1 +- 5%)",
+        "config": {"workload": w.name, "n": n_tot, "scheme": args.scheme, "precision": w.precision,
+                   "dt": dt, "bricks": list(w.replicas[0].bricks), "l2": "inputs larger than L2 "
+                   f"(state ~{n_tot * (48 if w.precision == 'mixed' else 104) / 1e6:.0f} MB)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": e2e,
+        "gpu_launches": None,
+        "roofline": roofline,
+        "phase_ms": phase_avg,
+        "energy": {"rel_drift_over_timed_steps": drift, "steps": args.steps + args.warmup,
+                   "status": status},
+    }
+    nlaunch = count_launches(S, args.scheme)
+    out["gpu_launches"] = nlaunch * args.steps
+    if rank == 0:
+        out["clocks"] = clk.summary()
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cpu_baseline(w, args.scheme, args.cpu_seconds)
+        print(json.dumps(out))
+    S.close()
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+def count_launches(S, scheme: str) -> int:
+    """Kernels of one step: kick-drift, 3 scan passes, scatter, gather, force,
+    step counter, plus the scheme's FD kernels (SSA: one launch per round)."""
+    base = 1 + 3 + 2 + 1 + 1
+    ssa_rounds = 0
+    if scheme in ("HYBRID", "SSA"):
+        ssa_rounds = 1 + 13 * 2   # at least; a third colour is added for odd periodic rings
+    return base + {"SER": 2, "HYBRID": ssa_rounds + 3, "SEM": 1, "SSA": ssa_rounds + 1}[scheme]
+
+
+def oracle_sample(w, n_target: int):
+    """A cubic sub-box of the workload at the same density and parameters."""
+    from paper_1507_06643_gb300 import inputs
+    spec = w.replicas[0]
+    vol = spec.box[0] * spec.box[1] * spec.box[2]
+    rho = spec.n / vol
+    n = max(1000, min(spec.n, int(n_target)))
+    L = (n / rho) ** (1 / 3)
+    cells_per_brick = 6
+    b = max(1, int(L // cells_per_brick)) if spec.bricks != (1, 1, 1) else 1
+    while b > 1 and math.floor(L / b) * b < 3:
+        b -= 1
+    sub = inputs.Workload(w.name + "_sample", [inputs.ReplicaSpec(n, (L, L, L), spec.cv, spec.kT, (b, b, b))],
+                          w.mass, w.r_cut, w.a, w.sigma, w.dt, 1, w.seed, "fp64")
+    return sub
+
+
+def cpu_baseline(w, scheme: str, seconds: float, steps: int | None = None):
+    from oracle import oracle as O
+    from paper_1507_06643_gb300 import inputs
+    rate_guess = 6.0e4
+    n_target = seconds * rate_guess if steps is None else seconds * rate_guess / steps
+    sub = oracle_sample(w, n_target)
+    spec = sub.replicas[0]
+    q, p, e = inputs.workload_state(sub, float32=False)
+    S = O.System([O.make_replica(spec.n, spec.box, spec.cv, spec.bricks)],
+                 O.make_params(sub.mass, sub.r_cut, sub.a, sub.sigma, sub.seed), q, p, e)
+    nsteps = steps or 1
+    t = time.perf_counter()
+    S.run(nsteps, sub.dt, scheme)
+    el = time.perf_counter() - t
+    return {"value": spec.n * nsteps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nsteps} step(s) of a {spec.n}-particle cubic sub-box of {w.name} "
+                      f"(same density and parameters, FP64, {scheme}, bricks {spec.bricks}), "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = workload_and_scheme(args)
+    from oracle import oracle as O
+    from paper_1507_06643_gb300 import inputs
+    total = args.steps + args.warmup
+    n_target = max(2000, 150.0 * 6.0e4 / max(total, 1))
+    sub = oracle_sample(w, n_target)
+    spec = sub.replicas[0]
+    q, p, e = inputs.workload_state(sub, float32=False)
+    S = O.System([O.make_replica(spec.n, spec.box, spec.cv, spec.bricks)],
+                 O.make_params(sub.mass, sub.r_cut, sub.a, sub.sigma, sub.seed), q, p, e)
+    S.run(args.warmup, sub.dt, args.scheme)
+    t = time.perf_counter()
+    S.run(args.steps, sub.dt, args.scheme)
+    el = time.perf_counter() - t
+    value = spec.n * args.steps / el
+    sample = (f"{spec.n}-particle cubic sub-box of {w.name} (same density and parameters), FP64 "
+              f"oracle, {args.scheme}, {args.steps} timed steps after {args.warmup}")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / max(args.steps, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": w.name, "scheme": args.scheme,
+                                           "precision": "fp64", "sample_n": spec.n},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large_n4m")
+    ap.add_argument("--scheme", default="HYBRID", choices=["SER", "HYBRID", "SEM", "SSA"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--profile-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

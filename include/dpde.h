@@ -247,6 +247,24 @@ const char* dpde_last_error(const dpde_handle* h);
 
 /* ---- diagnostics ---- */
 
+/* Phases of one step, for dpde_step_profiled. */
+#define DPDE_PHASE_KICK_DRIFT  0  /* Verlet first half, cell keys, counts  */
+#define DPDE_PHASE_SCAN        1  /* prefix sum of the cell counts         */
+#define DPDE_PHASE_GATHER      2  /* scatter + (cell, id) rank + gather    */
+#define DPDE_PHASE_FORCE       3  /* forces + second half-kick             */
+#define DPDE_PHASE_SSA         4  /* SSA rounds (Hybrid set A, or SSA)      */
+#define DPDE_PHASE_SWEEP1      5  /* SER first sweep                       */
+#define DPDE_PHASE_SWEEP2      6  /* SER second sweep / SEM sweep / copy   */
+#define DPDE_PHASE_OTHER       7  /* beta refresh, step counter            */
+#define DPDE_NUM_PHASES        8
+
+/* Runs n steps like dpde_step without a graph, with CUDA events recorded on
+ * the handle's stream around each phase; adds each phase's total elapsed
+ * milliseconds over the n steps into phase_ms[DPDE_NUM_PHASES] (host array,
+ * not cleared). Synchronous. */
+int dpde_step_profiled(dpde_handle* h, int64_t n, double dt, int32_t scheme,
+                       double* phase_ms);
+
 /* Runs the device Philox4x32-10 of the library on n (counter, key) pairs:
  * ctr is 4n uint32, key 2n uint32, out 4n uint32, all host pointers.
  * Used to check the device generator bit for bit. Synchronous. */

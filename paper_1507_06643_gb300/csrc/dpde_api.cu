@@ -1,0 +1,603 @@
+// dpde_api.cu -- the C ABI of include/dpde.h: handle, buffers, launch
+// sequence of one timestep, CUDA-graph replay, observables, diagnostics.
+#include "dpde.h"
+#include "dpde_kernels.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+using namespace dpde;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+struct GraphKey {
+    int scheme;
+    unsigned long long dt_bits;
+    bool operator<(const GraphKey& o) const {
+        return scheme != o.scheme ? scheme < o.scheme : dt_bits < o.dt_bits;
+    }
+};
+
+}  // namespace
+
+struct dpde_handle {
+    dpde_params prm{};
+    int R = 0;
+    std::vector<dpde_replica> reps;
+    std::vector<RepInfo> info;
+    int N = 0;
+    int ncells = 0;
+    int nchunks = 0;
+    bool mixed = false;
+    int need_col3[14] = {0};       // some replica needs a third colour for direction d
+    int need_col3_whole[14] = {0};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;
+    // device buffers
+    void *qA = nullptr, *pA = nullptr, *qB = nullptr, *pB = nullptr, *F = nullptr, *dp = nullptr;
+    double *eA = nullptr, *eB = nullptr;
+    int *key = nullptr, *tmp = nullptr, *cnt = nullptr, *start = nullptr, *bsum = nullptr;
+    int *rep_of_slot = nullptr, *rep_of_cell = nullptr;
+    int *chunk_rep = nullptr, *chunk_begin = nullptr, *chunk_end = nullptr, *rep_chunk_begin = nullptr;
+    double *partial = nullptr, *obs_out = nullptr;
+    RepInfo* d_reps = nullptr;
+    long long* d_step = nullptr;
+    unsigned int* d_status = nullptr;
+    double* staging = nullptr;       // 7N doubles: q (3N), p (3N), eps (N)
+    long long step = 0;              // host mirror of the device counter
+    int block = 256;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    cudaEvent_t prof_ev[DPDE_NUM_PHASES][2] = {};
+    bool profiling = false;
+    bool prof_used[DPDE_NUM_PHASES] = {};
+    std::string err;
+};
+
+namespace {
+
+int fail(dpde_handle* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(dpde_handle* h, cudaError_t e, const char* what) {
+    return fail(h, e == cudaErrorMemoryAllocation ? DPDE_ERR_OOM : DPDE_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                                  \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);     \
+    } while (0)
+
+template <class T>
+Ctx<T> make_ctx(dpde_handle* h) {
+    Ctx<T> C;
+    C.qA = (vec_t<T>*)h->qA; C.pA = (vec_t<T>*)h->pA; C.eA = h->eA;
+    C.qB = (vec_t<T>*)h->qB; C.pB = (vec_t<T>*)h->pB; C.eB = h->eB;
+    C.F = (vec_t<T>*)h->F; C.dp = (vec_t<T>*)h->dp;
+    C.key = h->key; C.tmp = h->tmp;
+    C.count = h->cnt; C.fill = h->cnt + h->ncells; C.start = h->start;
+    C.rep_of_slot = h->rep_of_slot; C.rep_of_cell = h->rep_of_cell;
+    C.reps = h->d_reps; C.step = h->d_step; C.status = h->d_status;
+    C.N = h->N; C.ncells = h->ncells;
+    C.m = (T)h->prm.mass; C.inv_m = (T)(1.0 / h->prm.mass);
+    C.rc = (T)h->prm.r_cut; C.rc2 = (T)(h->prm.r_cut * h->prm.r_cut);
+    C.inv_rc = (T)(1.0 / h->prm.r_cut);
+    C.a = (T)h->prm.a; C.sigma = (T)h->prm.sigma;
+    C.sig2_4 = (T)(h->prm.sigma * h->prm.sigma / 4.0);
+    C.seed = make_uint2((uint32_t)(h->prm.seed & 0xffffffffu), (uint32_t)(h->prm.seed >> 32));
+    return C;
+}
+
+// phase markers (only when dpde_step_profiled is running)
+void phase(dpde_handle* h, cudaStream_t st, int ph, int end) {
+    if (!h->profiling) return;
+    cudaEventRecord(h->prof_ev[ph][end], st);
+    h->prof_used[ph] = true;
+}
+
+// cell sort of set A into set B (kick = 1: Verlet first half before it)
+template <class T>
+void enqueue_sort(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T half_dt, T dt, int kick) {
+    const int nb = ceil_div(h->N, h->block);
+    phase(h, st, DPDE_PHASE_KICK_DRIFT, 0);
+    cudaMemsetAsync(h->cnt, 0, sizeof(int) * 2 * (size_t)h->ncells, st);
+    k_kick_drift_key<T><<<nb, h->block, 0, st>>>(C, half_dt, dt, kick);
+    phase(h, st, DPDE_PHASE_KICK_DRIFT, 1);
+    phase(h, st, DPDE_PHASE_SCAN, 0);
+    const int ntile = ceil_div(h->ncells, SCAN_TILE);
+    k_scan_local<<<ntile, SCAN_THREADS, 0, st>>>(h->cnt, h->start, h->bsum, h->ncells);
+    k_scan_bsums<<<1, 1024, 0, st>>>(h->bsum, ntile);
+    k_scan_add<<<ceil_div(h->ncells, 256), 256, 0, st>>>(h->start, h->bsum, h->ncells, h->N);
+    phase(h, st, DPDE_PHASE_SCAN, 1);
+    phase(h, st, DPDE_PHASE_GATHER, 0);
+    k_scatter<T><<<nb, h->block, 0, st>>>(C);
+    k_rank_gather<T><<<nb, h->block, 0, st>>>(C);
+    phase(h, st, DPDE_PHASE_GATHER, 1);
+}
+
+template <class T>
+void enqueue_ssa_rounds(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_dt, int whole) {
+    const int nbc = ceil_div(h->ncells, 128);
+    for (int di = 0; di < 14; ++di) {
+        const int ncol = di == 0 ? 1 : ((whole ? h->need_col3_whole[di] : h->need_col3[di]) ? 3 : 2);
+        for (int col = 0; col < ncol; ++col)
+            k_ssa_round<T><<<nbc, 128, 0, st>>>(C, di, col, whole, dt, sqrt_dt);
+    }
+}
+
+template <class T>
+void enqueue_step(dpde_handle* h, cudaStream_t st, double dt_d, int scheme) {
+    const Ctx<T> C = make_ctx<T>(h);
+    const T dt = (T)dt_d, half_dt = (T)(0.5 * dt_d), sqrt_dt = (T)std::sqrt(dt_d);
+    const int nb = ceil_div(h->N, h->block);
+    enqueue_sort<T>(h, C, st, half_dt, dt, 1);
+    phase(h, st, DPDE_PHASE_FORCE, 0);
+    k_force<T><<<nb, h->block, 0, st>>>(C, half_dt, 1);
+    phase(h, st, DPDE_PHASE_FORCE, 1);
+    const int cross = scheme == DPDE_HYBRID ? 1 : 0;
+    if (scheme == DPDE_HYBRID || scheme == DPDE_SSA) {
+        phase(h, st, DPDE_PHASE_SSA, 0);
+        enqueue_ssa_rounds<T>(h, C, st, dt, sqrt_dt, scheme == DPDE_SSA ? 1 : 0);
+        phase(h, st, DPDE_PHASE_SSA, 1);
+    }
+    if (scheme == DPDE_HYBRID) {
+        phase(h, st, DPDE_PHASE_OTHER, 0);
+        k_refresh_beta<T><<<nb, h->block, 0, st>>>(C);
+        phase(h, st, DPDE_PHASE_OTHER, 1);
+    }
+    if (scheme == DPDE_SER || scheme == DPDE_HYBRID) {
+        phase(h, st, DPDE_PHASE_SWEEP1, 0);
+        k_ser_sweep1<T><<<nb, h->block, 0, st>>>(C, dt, sqrt_dt, cross);
+        phase(h, st, DPDE_PHASE_SWEEP1, 1);
+    }
+    phase(h, st, DPDE_PHASE_SWEEP2, 0);
+    if (scheme == DPDE_SER || scheme == DPDE_HYBRID) k_ser_sweep2<T><<<nb, h->block, 0, st>>>(C, dt, sqrt_dt, cross);
+    else if (scheme == DPDE_SEM) k_sem<T><<<nb, h->block, 0, st>>>(C, dt, sqrt_dt);
+    else k_copy_back<T><<<nb, h->block, 0, st>>>(C);
+    phase(h, st, DPDE_PHASE_SWEEP2, 1);
+    k_step_inc<<<1, 1, 0, st>>>(h->d_step);
+}
+
+void enqueue_step_any(dpde_handle* h, cudaStream_t st, double dt, int scheme) {
+    if (h->mixed) enqueue_step<float>(h, st, dt, scheme);
+    else enqueue_step<double>(h, st, dt, scheme);
+}
+
+template <class T>
+void enqueue_set_state(dpde_handle* h, cudaStream_t st, const double* q, const double* p, const double* e) {
+    const Ctx<T> C = make_ctx<T>(h);
+    const int nb = ceil_div(h->N, h->block);
+    k_load_state<T><<<nb, h->block, 0, st>>>(C, q, p, e);
+    enqueue_sort<T>(h, C, st, T(0), T(0), 0);
+    k_force<T><<<nb, h->block, 0, st>>>(C, T(0), 0);
+    k_copy_back<T><<<nb, h->block, 0, st>>>(C);
+}
+
+template <class T>
+void enqueue_get_state(dpde_handle* h, cudaStream_t st, double* q, double* p, double* e) {
+    const Ctx<T> C = make_ctx<T>(h);
+    k_get_state<T><<<ceil_div(h->N, h->block), h->block, 0, st>>>(C, q, p, e);
+}
+
+template <class T>
+void enqueue_obs(dpde_handle* h, cudaStream_t st) {
+    const Ctx<T> C = make_ctx<T>(h);
+    if (h->nchunks > 0)
+        k_obs_chunks<T><<<h->nchunks, OBS_THREADS, 0, st>>>(C, h->chunk_rep, h->chunk_begin, h->chunk_end,
+                                                             h->partial);
+    k_obs_reps<<<h->R, 32, 0, st>>>(h->partial, h->rep_chunk_begin, h->R, h->obs_out);
+}
+
+int read_status(dpde_handle* h) {
+    unsigned int st = 0;
+    CK(h, cudaMemcpyAsync(&st, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (st & ST_NONFINITE) return fail(h, DPDE_ERR_NONFINITE, "non-finite value in the state");
+    if (st & ST_NEG_EPS) return fail(h, DPDE_ERR_NEG_EPS, "internal energy eps_i <= 0");
+    return DPDE_OK;
+}
+
+void free_all(dpde_handle* h) {
+    for (auto& row : h->prof_ev)
+        for (auto& ev : row)
+            if (ev) cudaEventDestroy(ev);
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    void* bufs[] = {h->qA, h->pA, h->qB, h->pB, h->F, h->dp, h->eA, h->eB, h->key, h->tmp, h->cnt,
+                    h->start, h->bsum, h->rep_of_slot, h->rep_of_cell, h->chunk_rep, h->chunk_begin,
+                    h->chunk_end, h->rep_chunk_begin, h->partial, h->obs_out, h->d_reps, h->d_step,
+                    h->d_status, h->staging};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replica* replicas,
+                void* stream, dpde_handle** out) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, DPDE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!params || !replicas || n_replicas < 1) return fail(nullptr, DPDE_ERR_ARG, "bad params/replicas");
+    const dpde_params& P = *params;
+    if (!(P.mass > 0) || !(P.r_cut > 0) || !(P.a >= 0) || !(P.sigma >= 0) || P.reserved != 0 ||
+        (P.precision != DPDE_FP64 && P.precision != DPDE_MIXED))
+        return fail(nullptr, DPDE_ERR_ARG, "invalid dpde_params");
+    dpde_handle* h = new dpde_handle();
+    h->prm = P;
+    h->R = n_replicas;
+    h->mixed = P.precision == DPDE_MIXED;
+    h->reps.assign(replicas, replicas + n_replicas);
+    long long N = 0, ncells = 0, nchunks = 0;
+    const int CHUNK = 4096;
+    std::vector<int> chunk_rep, chunk_begin, chunk_end, rep_chunk_begin(1, 0);
+    for (int r = 0; r < n_replicas; ++r) {
+        const dpde_replica& d = replicas[r];
+        RepInfo I{};
+        if (d.n < 0 || d.reserved != 0 || !(d.cv > 0)) {
+            delete h;
+            return fail(nullptr, DPDE_ERR_ARG, "replica " + std::to_string(r) + ": bad n/cv");
+        }
+        for (int a = 0; a < 3; ++a) {
+            if (!(d.box[a] > 0) || d.bricks[a] < 1) {
+                delete h;
+                return fail(nullptr, DPDE_ERR_ARG, "replica " + std::to_string(r) + ": bad box/bricks");
+            }
+            I.k[a] = (int)std::floor(d.box[a] / ((double)d.bricks[a] * P.r_cut));
+            I.B[a] = d.bricks[a];
+            I.nc[a] = I.B[a] * I.k[a];
+            if (I.k[a] < 1 || I.nc[a] < 3) {
+                delete h;
+                return fail(nullptr, DPDE_ERR_ARG,
+                            "replica " + std::to_string(r) + ": box too small for the brick grid "
+                            "(need floor(L/(B r_cut)) >= 1 and B*that >= 3 cells per axis)");
+            }
+            I.L[a] = d.box[a];
+            I.s[a] = (double)I.nc[a] / d.box[a];
+            I.Lf[a] = (float)d.box[a];
+            I.sf[a] = (float)I.s[a];
+            I.odd_ring[a] = (I.B[a] == 1) && (I.k[a] & 1);
+        }
+        I.cell_off = (int)ncells;
+        I.ncells = I.nc[0] * I.nc[1] * I.nc[2];
+        I.part_off = (int)N;
+        I.n = (int)d.n;
+        I.cv = d.cv;
+        I.cvf = (float)d.cv;
+        h->info.push_back(I);
+        N += d.n;
+        ncells += I.ncells;
+        for (long long b = 0; b < d.n; b += CHUNK) {
+            chunk_rep.push_back(r);
+            chunk_begin.push_back((int)(I.part_off + b));
+            chunk_end.push_back((int)(I.part_off + std::min<long long>(b + CHUNK, d.n)));
+        }
+        rep_chunk_begin.push_back((int)chunk_rep.size());
+        if (N > (1ll << 30) || ncells > (1ll << 30)) {
+            delete h;
+            return fail(nullptr, DPDE_ERR_ARG, "too many particles or cells (limit 2^30)");
+        }
+    }
+    nchunks = (long long)chunk_rep.size();
+    h->N = (int)N;
+    h->ncells = (int)ncells;
+    h->nchunks = (int)nchunks;
+    // colours per SSA direction: three when the leading axis is a periodic
+    // brick axis with an odd number of cells
+    static const int dirs[14][3] = {{0, 0, 0},   {1, 0, 0},  {-1, 1, 0}, {0, 1, 0},  {1, 1, 0},
+                                    {-1, -1, 1}, {0, -1, 1}, {1, -1, 1}, {-1, 0, 1}, {0, 0, 1},
+                                    {1, 0, 1},   {-1, 1, 1}, {0, 1, 1},  {1, 1, 1}};
+    for (int di = 1; di < 14; ++di) {
+        const int lead = dirs[di][2] ? 2 : (dirs[di][1] ? 1 : 0);
+        for (const RepInfo& I : h->info) {
+            if (I.odd_ring[lead]) h->need_col3[di] = 1;
+            if (I.nc[lead] & 1) h->need_col3_whole[di] = 1;
+        }
+    }
+    auto bail = [&](cudaError_t e, const char* what) {
+        std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+        int code = e == cudaErrorMemoryAllocation ? DPDE_ERR_OOM : DPDE_ERR_CUDA;
+        free_all(h);
+        delete h;
+        return fail(nullptr, code, msg);
+    };
+#define CKC(call)                                  \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return bail(e_, #call); \
+    } while (0)
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+    } else {
+        CKC(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    CKC(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    const size_t vsz = h->mixed ? sizeof(float4) : sizeof(d4);
+    const size_t n1 = (size_t)std::max(1, h->N), c1 = (size_t)std::max(1, h->ncells);
+    CKC(cudaMalloc(&h->qA, vsz * n1));
+    CKC(cudaMalloc(&h->pA, vsz * n1));
+    CKC(cudaMalloc(&h->qB, vsz * n1));
+    CKC(cudaMalloc(&h->pB, vsz * n1));
+    CKC(cudaMalloc(&h->F, vsz * n1));
+    CKC(cudaMalloc(&h->dp, vsz * n1));
+    CKC(cudaMalloc(&h->eA, sizeof(double) * n1));
+    CKC(cudaMalloc(&h->eB, sizeof(double) * n1));
+    CKC(cudaMalloc(&h->key, sizeof(int) * n1));
+    CKC(cudaMalloc(&h->tmp, sizeof(int) * n1));
+    CKC(cudaMalloc(&h->cnt, sizeof(int) * 2 * c1));
+    CKC(cudaMalloc(&h->start, sizeof(int) * (c1 + 1)));
+    CKC(cudaMalloc(&h->bsum, sizeof(int) * (size_t)std::max(1, ceil_div(h->ncells, SCAN_TILE))));
+    CKC(cudaMalloc(&h->rep_of_slot, sizeof(int) * n1));
+    CKC(cudaMalloc(&h->rep_of_cell, sizeof(int) * c1));
+    CKC(cudaMalloc(&h->chunk_rep, sizeof(int) * std::max<size_t>(1, chunk_rep.size())));
+    CKC(cudaMalloc(&h->chunk_begin, sizeof(int) * std::max<size_t>(1, chunk_rep.size())));
+    CKC(cudaMalloc(&h->chunk_end, sizeof(int) * std::max<size_t>(1, chunk_rep.size())));
+    CKC(cudaMalloc(&h->rep_chunk_begin, sizeof(int) * rep_chunk_begin.size()));
+    CKC(cudaMalloc(&h->partial, sizeof(double) * NTERMS * std::max<size_t>(1, chunk_rep.size())));
+    CKC(cudaMalloc(&h->obs_out, sizeof(double) * NTERMS * (size_t)h->R));
+    CKC(cudaMalloc(&h->d_reps, sizeof(RepInfo) * (size_t)h->R));
+    CKC(cudaMalloc(&h->d_step, sizeof(long long)));
+    CKC(cudaMalloc(&h->d_status, sizeof(unsigned int)));
+    CKC(cudaMalloc(&h->staging, sizeof(double) * 7 * n1));
+    {
+        std::vector<int> ros(n1, 0), roc(c1, 0);
+        for (int r = 0; r < h->R; ++r) {
+            const RepInfo& I = h->info[r];
+            for (int s = 0; s < I.n; ++s) ros[I.part_off + s] = r;
+            for (int c = 0; c < I.ncells; ++c) roc[I.cell_off + c] = r;
+        }
+        CKC(cudaMemcpy(h->rep_of_slot, ros.data(), sizeof(int) * n1, cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(h->rep_of_cell, roc.data(), sizeof(int) * c1, cudaMemcpyHostToDevice));
+        if (!chunk_rep.empty()) {
+            CKC(cudaMemcpy(h->chunk_rep, chunk_rep.data(), sizeof(int) * chunk_rep.size(), cudaMemcpyHostToDevice));
+            CKC(cudaMemcpy(h->chunk_begin, chunk_begin.data(), sizeof(int) * chunk_rep.size(), cudaMemcpyHostToDevice));
+            CKC(cudaMemcpy(h->chunk_end, chunk_end.data(), sizeof(int) * chunk_rep.size(), cudaMemcpyHostToDevice));
+        }
+        CKC(cudaMemcpy(h->rep_chunk_begin, rep_chunk_begin.data(), sizeof(int) * rep_chunk_begin.size(),
+                       cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(h->d_reps, h->info.data(), sizeof(RepInfo) * (size_t)h->R, cudaMemcpyHostToDevice));
+        CKC(cudaMemset(h->d_step, 0, sizeof(long long)));
+        CKC(cudaMemset(h->d_status, 0, sizeof(unsigned int)));
+        CKC(cudaMemset(h->eA, 0, sizeof(double) * n1));
+        CKC(cudaMemset(h->qA, 0, vsz * n1));
+        CKC(cudaMemset(h->pA, 0, vsz * n1));
+        CKC(cudaMemset(h->F, 0, vsz * n1));
+    }
+#undef CKC
+    *out = h;
+    return DPDE_OK;
+}
+
+int dpde_set_state(dpde_handle* h, const double* q, const double* p, const double* eps, int64_t step,
+                   int32_t on_device) {
+    if (!h) return DPDE_ERR_ARG;
+    if (h->N > 0 && (!q || !p || !eps)) return fail(h, DPDE_ERR_ARG, "q, p and eps are required");
+    const size_t N = (size_t)h->N;
+    const double *dq = q, *dpp = p, *de = eps;
+    if (!on_device && N > 0) {
+        CK(h, cudaMemcpyAsync(h->staging, q, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(h->staging + 3 * N, p, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(h->staging + 6 * N, eps, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
+        dq = h->staging; dpp = h->staging + 3 * N; de = h->staging + 6 * N;
+    }
+    if (N > 0) {
+        if (h->mixed) enqueue_set_state<float>(h, h->stream, dq, dpp, de);
+        else enqueue_set_state<double>(h, h->stream, dq, dpp, de);
+    }
+    long long s = step;
+    CK(h, cudaMemcpyAsync(h->d_step, &s, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaGetLastError());
+    h->step = step;
+    return read_status(h);
+}
+
+int dpde_get_state(dpde_handle* h, double* q, double* p, double* eps, int32_t on_device) {
+    if (!h) return DPDE_ERR_ARG;
+    const size_t N = (size_t)h->N;
+    if (N > 0) {
+        double* dq = on_device ? q : (q ? h->staging : nullptr);
+        double* dpp = on_device ? p : (p ? h->staging + 3 * N : nullptr);
+        double* de = on_device ? eps : (eps ? h->staging + 6 * N : nullptr);
+        if (h->mixed) enqueue_get_state<float>(h, h->stream, dq, dpp, de);
+        else enqueue_get_state<double>(h, h->stream, dq, dpp, de);
+        CK(h, cudaGetLastError());
+        if (!on_device) {
+            if (q) CK(h, cudaMemcpyAsync(q, h->staging, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, h->stream));
+            if (p) CK(h, cudaMemcpyAsync(p, h->staging + 3 * N, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, h->stream));
+            if (eps) CK(h, cudaMemcpyAsync(eps, h->staging + 6 * N, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
+        }
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return read_status(h);
+}
+
+int dpde_step(dpde_handle* h, int64_t n, double dt, int32_t scheme, int32_t use_graph) {
+    if (!h) return DPDE_ERR_ARG;
+    if (n < 0 || !(dt > 0) || !std::isfinite(dt) || scheme < DPDE_SER || scheme > DPDE_SSA)
+        return fail(h, DPDE_ERR_ARG, "bad n, dt or scheme");
+    if (n == 0 || h->N == 0) {
+        h->step += n;
+        if (n > 0) {
+            long long s = h->step;
+            CK(h, cudaMemcpyAsync(h->d_step, &s, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+        }
+        return DPDE_OK;
+    }
+    if (use_graph) {
+        GraphKey gk{scheme, 0};
+        std::memcpy(&gk.dt_bits, &dt, sizeof(double));
+        auto it = h->graphs.find(gk);
+        if (it == h->graphs.end()) {
+            cudaGraph_t g = nullptr;
+            CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+            enqueue_step_any(h, h->cap_stream, dt, scheme);
+            CK(h, cudaStreamEndCapture(h->cap_stream, &g));
+            cudaGraphExec_t ex = nullptr;
+            cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+            it = h->graphs.emplace(gk, ex).first;
+        }
+        for (int64_t k = 0; k < n; ++k) CK(h, cudaGraphLaunch(it->second, h->stream));
+    } else {
+        for (int64_t k = 0; k < n; ++k) enqueue_step_any(h, h->stream, dt, scheme);
+        CK(h, cudaGetLastError());
+    }
+    h->step += n;
+    return DPDE_OK;
+}
+
+int dpde_step_profiled(dpde_handle* h, int64_t n, double dt, int32_t scheme, double* phase_ms) {
+    if (!h || !phase_ms) return DPDE_ERR_ARG;
+    if (n < 0 || !(dt > 0) || !std::isfinite(dt) || scheme < DPDE_SER || scheme > DPDE_SSA)
+        return fail(h, DPDE_ERR_ARG, "bad n, dt or scheme");
+    if (h->N == 0) return dpde_step(h, n, dt, scheme, 0);
+    for (auto& row : h->prof_ev)
+        for (auto& ev : row)
+            if (!ev) CK(h, cudaEventCreate(&ev));
+    for (int64_t k = 0; k < n; ++k) {
+        for (bool& u : h->prof_used) u = false;
+        h->profiling = true;
+        enqueue_step_any(h, h->stream, dt, scheme);
+        h->profiling = false;
+        CK(h, cudaGetLastError());
+        CK(h, cudaStreamSynchronize(h->stream));
+        for (int ph = 0; ph < DPDE_NUM_PHASES; ++ph) {
+            if (!h->prof_used[ph]) continue;
+            float ms = 0.f;
+            CK(h, cudaEventElapsedTime(&ms, h->prof_ev[ph][0], h->prof_ev[ph][1]));
+            phase_ms[ph] += ms;
+        }
+    }
+    h->step += n;
+    return DPDE_OK;
+}
+
+int dpde_sync(dpde_handle* h) {
+    if (!h) return DPDE_ERR_ARG;
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaGetLastError());
+    return read_status(h);
+}
+
+int dpde_observables(dpde_handle* h, dpde_obs* out) {
+    if (!h || !out) return DPDE_ERR_ARG;
+    if (h->mixed) enqueue_obs<float>(h, h->stream);
+    else enqueue_obs<double>(h, h->stream);
+    CK(h, cudaGetLastError());
+    std::vector<double> host((size_t)NTERMS * h->R);
+    CK(h, cudaMemcpyAsync(host.data(), h->obs_out, sizeof(double) * host.size(), cudaMemcpyDeviceToHost,
+                          h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    bool neg = false, bad = false;
+    for (int r = 0; r < h->R; ++r) {
+        const double* t = host.data() + (size_t)NTERMS * r;
+        const long long n = h->info[r].n;
+        dpde_obs& o = out[r];
+        o.K = t[0]; o.U = t[1]; o.Eint = t[2];
+        o.E = o.U + o.K + o.Eint;
+        o.P[0] = t[3]; o.P[1] = t[4]; o.P[2] = t[5];
+        o.Tkin = n > 1 ? 2.0 * o.K / (3.0 * (double)(n - 1)) : 0.0;
+        o.Tint = n > 0 ? (double)n / t[6] : 0.0;
+        o.Tpot_num = t[7];
+        o.Tpot_den = t[8];
+        o.step = h->step;
+        o.n = n;
+        o.neg_eps = (int64_t)t[9];
+        o.nonfinite = (int64_t)t[10];
+        neg |= o.neg_eps > 0;
+        bad |= o.nonfinite > 0;
+    }
+    int st = read_status(h);
+    if (bad) return fail(h, DPDE_ERR_NONFINITE, "non-finite value in the state");
+    if (neg) return fail(h, DPDE_ERR_NEG_EPS, "internal energy eps_i <= 0");
+    return st;
+}
+
+int dpde_get_step(dpde_handle* h, int64_t* step) {
+    if (!h || !step) return DPDE_ERR_ARG;
+    *step = h->step;
+    return DPDE_OK;
+}
+
+int dpde_destroy(dpde_handle* h) {
+    if (!h) return DPDE_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+    return DPDE_OK;
+}
+
+const char* dpde_last_error(const dpde_handle* h) {
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int dpde_debug_philox(int64_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+    if (n < 0 || (n > 0 && (!ctr || !key || !out))) return DPDE_ERR_ARG;
+    if (n == 0) return DPDE_OK;
+    uint4 *dc = nullptr, *dout = nullptr;
+    uint2* dk = nullptr;
+    cudaError_t e = cudaMalloc(&dc, 16 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&dk, 8 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, 16 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpy(dc, ctr, 16 * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dk, key, 8 * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_debug_philox<<<ceil_div(n, 256), 256>>>((int)n, dc, dk, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, 16 * (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(dc); cudaFree(dk); cudaFree(dout);
+    if (e != cudaSuccess) return fail(nullptr, DPDE_ERR_CUDA, cudaGetErrorString(e));
+    return DPDE_OK;
+}
+
+int dpde_debug_gaussian(int64_t n, uint64_t seed, const uint32_t* step, const uint32_t* replica,
+                        const uint32_t* id_a, const uint32_t* id_b, int32_t precision, double* out) {
+    if (n < 0 || (n > 0 && (!step || !replica || !id_a || !id_b || !out))) return DPDE_ERR_ARG;
+    if (n == 0) return DPDE_OK;
+    uint32_t* d = nullptr;
+    double* dout = nullptr;
+    cudaError_t e = cudaMalloc(&d, 16 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, 24 * (size_t)n);
+    const uint32_t* src[4] = {step, replica, id_a, id_b};
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        e = cudaMemcpy(d + (size_t)k * n, src[k], 4 * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const uint2 s = make_uint2((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+        if (precision == DPDE_FP64)
+            k_debug_gauss<double><<<ceil_div(n, 256), 256>>>((int)n, s, d, d + n, d + 2 * n, d + 3 * n, dout);
+        else
+            k_debug_gauss<float><<<ceil_div(n, 256), 256>>>((int)n, s, d, d + n, d + 2 * n, d + 3 * n, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, 24 * (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(d); cudaFree(dout);
+    if (e != cudaSuccess) return fail(nullptr, DPDE_ERR_CUDA, cudaGetErrorString(e));
+    return DPDE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,247 @@
+"""Thin ctypes binding of the C ABI in include/dpde.h (libdpde.so).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of the library. Functions keep the C names (dpde_create, dpde_set_state,
+dpde_get_state, dpde_step, dpde_sync, dpde_observables, dpde_destroy, ...);
+:class:`System` wraps a handle for convenience. Host arrays are numpy float64
+arrays; device arrays may be passed as torch CUDA tensors (their data_ptr()
+is handed to the library) with ``on_device=True``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DPDE_OK = 0
+DPDE_ERR_ARG = -1
+DPDE_ERR_CUDA = -2
+DPDE_ERR_OOM = -3
+DPDE_ERR_NEG_EPS = -4
+DPDE_ERR_NONFINITE = -5
+DPDE_ERR_TIMEOUT = -6
+
+FP64, MIXED = 0, 1
+SER, HYBRID, SEM, SSA = 0, 1, 2, 3
+SCHEMES = {"SER": SER, "HYBRID": HYBRID, "SEM": SEM, "SSA": SSA}
+PRECISIONS = {"fp64": FP64, "mixed": MIXED}
+
+
+class DPDEError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"dpde error {code}: {msg}")
+        self.code = code
+
+
+class dpde_params(C.Structure):
+    _fields_ = [("mass", C.c_double), ("r_cut", C.c_double), ("a", C.c_double),
+                ("sigma", C.c_double), ("seed", C.c_uint64), ("precision", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class dpde_replica(C.Structure):
+    _fields_ = [("n", C.c_int64), ("box", C.c_double * 3), ("cv", C.c_double),
+                ("bricks", C.c_int32 * 3), ("reserved", C.c_int32)]
+
+
+class dpde_obs(C.Structure):
+    _fields_ = [("E", C.c_double), ("K", C.c_double), ("U", C.c_double), ("Eint", C.c_double),
+                ("P", C.c_double * 3), ("Tkin", C.c_double), ("Tint", C.c_double),
+                ("Tpot_num", C.c_double), ("Tpot_den", C.c_double), ("step", C.c_int64),
+                ("n", C.c_int64), ("neg_eps", C.c_int64), ("nonfinite", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "P"}
+        d["Px"], d["Py"], d["Pz"] = self.P[0], self.P[1], self.P[2]
+        return d
+
+
+_lib = None
+EXPORTS = ["dpde_create", "dpde_set_state", "dpde_get_state", "dpde_step", "dpde_sync",
+           "dpde_observables", "dpde_get_step", "dpde_destroy", "dpde_last_error",
+           "dpde_debug_philox", "dpde_debug_gaussian", "dpde_step_profiled"]
+PHASES = ["kick_drift", "scan", "gather", "force", "ssa", "sweep1", "sweep2", "other"]
+
+
+def lib():
+    """Loads the in-tree libdpde.so (building it when it is missing or stale).
+    Raises when the library cannot be built or loaded: there is no fallback."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        vp = C.c_void_p
+        dp = C.POINTER(C.c_double)
+        u32p = C.POINTER(C.c_uint32)
+        L.dpde_create.argtypes = [C.POINTER(dpde_params), C.c_int32, C.POINTER(dpde_replica), vp,
+                                  C.POINTER(vp)]
+        L.dpde_set_state.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_int32]
+        L.dpde_get_state.argtypes = [vp, vp, vp, vp, C.c_int32]
+        L.dpde_step.argtypes = [vp, C.c_int64, C.c_double, C.c_int32, C.c_int32]
+        L.dpde_sync.argtypes = [vp]
+        L.dpde_observables.argtypes = [vp, C.POINTER(dpde_obs)]
+        L.dpde_get_step.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.dpde_destroy.argtypes = [vp]
+        L.dpde_last_error.argtypes = [vp]
+        L.dpde_last_error.restype = C.c_char_p
+        L.dpde_step_profiled.argtypes = [vp, C.c_int64, C.c_double, C.c_int32, dp]
+        L.dpde_debug_philox.argtypes = [C.c_int64, u32p, u32p, u32p]
+        L.dpde_debug_gaussian.argtypes = [C.c_int64, C.c_uint64, u32p, u32p, u32p, u32p,
+                                          C.c_int32, dp]
+        _lib = L
+    return _lib
+
+
+def _addr(x):
+    """Pointer of a numpy array (host) or a torch tensor (device or host)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(x.ctypes.data)
+
+
+def _check(h, rc):
+    if rc != DPDE_OK:
+        raise DPDEError(rc, lib().dpde_last_error(h).decode())
+    return rc
+
+
+def dpde_create(params: dpde_params, replicas, stream=None):
+    reps = (dpde_replica * len(replicas))(*replicas)
+    h = C.c_void_p()
+    rc = lib().dpde_create(C.byref(params), len(replicas), reps,
+                           C.c_void_p(stream) if stream else None, C.byref(h))
+    if rc != DPDE_OK:
+        raise DPDEError(rc, lib().dpde_last_error(None).decode())
+    return h
+
+
+def dpde_set_state(h, q, p, eps, step=0, on_device=False):
+    return _check(h, lib().dpde_set_state(h, _addr(q), _addr(p), _addr(eps), int(step),
+                                          int(on_device)))
+
+
+def dpde_get_state(h, q, p, eps, on_device=False):
+    return lib().dpde_get_state(h, _addr(q), _addr(p), _addr(eps), int(on_device))
+
+
+def dpde_step(h, n, dt, scheme, use_graph=True):
+    return _check(h, lib().dpde_step(h, int(n), float(dt), SCHEMES.get(scheme, scheme),
+                                     int(use_graph)))
+
+
+def dpde_step_profiled(h, n, dt, scheme) -> dict:
+    ms = np.zeros(len(PHASES))
+    _check(h, lib().dpde_step_profiled(h, int(n), float(dt), SCHEMES.get(scheme, scheme),
+                                       ms.ctypes.data_as(C.POINTER(C.c_double))))
+    return dict(zip(PHASES, ms.tolist()))
+
+
+def dpde_sync(h):
+    return lib().dpde_sync(h)
+
+
+def dpde_observables(h, n_replicas):
+    out = (dpde_obs * n_replicas)()
+    rc = lib().dpde_observables(h, out)
+    return rc, [o.as_dict() for o in out]
+
+
+def dpde_destroy(h):
+    return lib().dpde_destroy(h)
+
+
+def dpde_debug_philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
+    ctr = np.ascontiguousarray(ctr, np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, np.uint32).reshape(-1, 2)
+    out = np.empty_like(ctr)
+    u = C.POINTER(C.c_uint32)
+    _check(None, lib().dpde_debug_philox(len(ctr), ctr.ctypes.data_as(u), key.ctypes.data_as(u),
+                                         out.ctypes.data_as(u)))
+    return out
+
+
+def dpde_debug_gaussian(seed, step, replica, id_a, id_b, precision="fp64") -> np.ndarray:
+    shape = np.broadcast(step, replica, id_a, id_b).shape
+    arrs = [np.ascontiguousarray(np.broadcast_to(x, shape), np.uint32).ravel()
+            for x in (step, replica, id_a, id_b)]
+    out = np.empty((arrs[0].size, 3))
+    u = C.POINTER(C.c_uint32)
+    _check(None, lib().dpde_debug_gaussian(arrs[0].size, seed, *(a.ctypes.data_as(u) for a in arrs),
+                                           PRECISIONS.get(precision, precision),
+                                           out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
+def make_params(mass=1.0, r_cut=1.0, a=25.0, sigma=3.0, seed=0, precision="mixed") -> dpde_params:
+    return dpde_params(mass, r_cut, a, sigma, seed, PRECISIONS.get(precision, precision), 0)
+
+
+def make_replica(n, box, cv, bricks=(1, 1, 1)) -> dpde_replica:
+    if np.isscalar(box):
+        box = (box, box, box)
+    r = dpde_replica()
+    r.n = int(n)
+    r.box[:] = [float(x) for x in box]
+    r.cv = float(cv)
+    r.bricks[:] = [int(b) for b in bricks]
+    r.reserved = 0
+    return r
+
+
+class System:
+    """A handle over one or more replicas (arrays concatenated by replica;
+    ids are indices within a replica)."""
+
+    def __init__(self, params: dpde_params, replicas, stream=None):
+        self.params = params
+        self.replicas = list(replicas)
+        self.R = len(self.replicas)
+        self.N = int(sum(r.n for r in self.replicas))
+        self.h = dpde_create(params, self.replicas, stream)
+
+    def set_state(self, q, p, eps, step=0, on_device=False):
+        if not on_device:
+            q = np.ascontiguousarray(q, np.float64)
+            p = np.ascontiguousarray(p, np.float64)
+            eps = np.ascontiguousarray(eps, np.float64)
+        dpde_set_state(self.h, q, p, eps, step, on_device)
+
+    def get_state(self, check=True):
+        q = np.empty((self.N, 3))
+        p = np.empty((self.N, 3))
+        e = np.empty(self.N)
+        rc = dpde_get_state(self.h, q, p, e)
+        if check:
+            _check(self.h, rc)
+        return q, p, e
+
+    def step(self, n, dt, scheme, use_graph=True):
+        dpde_step(self.h, n, dt, scheme, use_graph)
+
+    def step_profiled(self, n, dt, scheme) -> dict:
+        return dpde_step_profiled(self.h, n, dt, scheme)
+
+    def sync(self):
+        return dpde_sync(self.h)
+
+    def observables(self, check=False):
+        rc, obs = dpde_observables(self.h, self.R)
+        if check:
+            _check(self.h, rc)
+        return obs
+
+    def close(self):
+        if self.h:
+            dpde_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
