@@ -90,7 +90,7 @@
  * ---------------------------------------------------------------------------
  *  For a replica with box L and brick grid B = (B_x, B_y, B_z):
  *       k_d     = floor(L_d / (B_d r_cut))   cells per brick along d (>= 1)
- *       ncell_d = B_d k_d                     (must be >= 3)
+ *       ncell_d = B_d k_d                     (must be >= 3 and <= 1024)
  *       c_d(x)  = min(ncell_d - 1, (int)(x * (ncell_d / L_d)))
  *       brick_d = c_d / k_d
  *  The quotient ncell_d / L_d is formed once in double. A pair is "intra
@@ -138,6 +138,10 @@ extern "C" {
                                       the state was advanced, nothing clamped */
 #define DPDE_ERR_NONFINITE     -5  /* NaN/Inf in the state                    */
 #define DPDE_ERR_TIMEOUT       -6  /* a bounded device wait gave up           */
+#define DPDE_ERR_CAPACITY      -7  /* a particle had more neighbours than the
+                                      list holds (density far above the one
+                                      the handle was sized for); the step's
+                                      FD part is invalid                      */
 
 /* ---- enumerations ---- */
 #define DPDE_FP64   0
@@ -235,6 +239,16 @@ int dpde_sync(dpde_handle* h);
  * such values (out is still filled). */
 int dpde_observables(dpde_handle* h, dpde_obs* out);
 
+/* Raw checkpoint of the internal state (positions as cell + offset, momenta,
+ * internal energies, forces, step counter) for a bit-exact restart.
+ * dpde_checkpoint: with buf == NULL stores the required size in *size;
+ * otherwise writes *size bytes to the host buffer buf. dpde_restore loads a
+ * checkpoint made by a handle of identical parameters and replicas (checked:
+ * DPDE_ERR_ARG otherwise). dpde_get_state / dpde_set_state round-trip
+ * through absolute coordinates and are exact only to rounding. Synchronous. */
+int dpde_checkpoint(dpde_handle* h, void* buf, uint64_t* size);
+int dpde_restore(dpde_handle* h, const void* buf, uint64_t size);
+
 /* Current step counter (steps since dpde_set_state plus its `step`). */
 int dpde_get_step(dpde_handle* h, int64_t* step);
 
@@ -264,6 +278,11 @@ const char* dpde_last_error(const dpde_handle* h);
  * not cleared). Synchronous. */
 int dpde_step_profiled(dpde_handle* h, int64_t n, double dt, int32_t scheme,
                        double* phase_ms);
+
+/* Cell coordinates (cx, cy, cz) of every particle in id order (3N int32,
+ * host pointer), as the library binned them at the end of the last step.
+ * Synchronous. */
+int dpde_get_cells(dpde_handle* h, int32_t* cells);
 
 /* Runs the device Philox4x32-10 of the library on n (counter, key) pairs:
  * ctr is 4n uint32, key 2n uint32, out 4n uint32, all host pointers.

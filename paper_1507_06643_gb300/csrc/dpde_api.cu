@@ -3,6 +3,7 @@
 #include "dpde.h"
 #include "dpde_kernels.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -27,6 +28,8 @@ struct GraphKey {
     }
 };
 
+constexpr int SSA_RCAP = 1024;   // pairs of one SSA round buffered per brick
+
 }  // namespace
 
 struct dpde_handle {
@@ -36,24 +39,31 @@ struct dpde_handle {
     std::vector<RepInfo> info;
     int N = 0;
     int ncells = 0;
+    int nbricks = 0;
     int nchunks = 0;
+    int kc_max = 1;
+    int ssa_cap = 0;          // particles per brick staged in shared memory
+    size_t ssa_smem = 0;
+    int nbr_cap = 0;
     bool mixed = false;
-    int need_col3[14] = {0};       // some replica needs a third colour for direction d
     int need_col3_whole[14] = {0};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t cap_stream = nullptr;
     // device buffers
     void *qA = nullptr, *pA = nullptr, *qB = nullptr, *pB = nullptr, *F = nullptr, *dp = nullptr;
-    double *eA = nullptr, *eB = nullptr;
+    void *eA = nullptr, *eB = nullptr, *nbr_w = nullptr;
+    int *cA = nullptr, *cB = nullptr, *nbr_j = nullptr, *nbr_n = nullptr;
+    uint32_t* idB = nullptr;
     int *key = nullptr, *tmp = nullptr, *cnt = nullptr, *start = nullptr, *bsum = nullptr;
-    int *rep_of_slot = nullptr, *rep_of_cell = nullptr;
+    int *rep_of_slot = nullptr, *rep_of_cell = nullptr, *brick_rep = nullptr, *tab = nullptr;
     int *chunk_rep = nullptr, *chunk_begin = nullptr, *chunk_end = nullptr, *rep_chunk_begin = nullptr;
     double *partial = nullptr, *obs_out = nullptr;
     RepInfo* d_reps = nullptr;
     long long* d_step = nullptr;
     unsigned int* d_status = nullptr;
     double* staging = nullptr;       // 7N doubles: q (3N), p (3N), eps (N)
+    int* cells_out = nullptr;        // 3N ints (diagnostic)
     long long step = 0;              // host mirror of the device counter
     int block = 256;
     std::map<GraphKey, cudaGraphExec_t> graphs;
@@ -85,12 +95,17 @@ int cuda_fail(dpde_handle* h, cudaError_t e, const char* what) {
 template <class T>
 Ctx<T> make_ctx(dpde_handle* h) {
     Ctx<T> C;
-    C.qA = (vec_t<T>*)h->qA; C.pA = (vec_t<T>*)h->pA; C.eA = h->eA;
-    C.qB = (vec_t<T>*)h->qB; C.pB = (vec_t<T>*)h->pB; C.eB = h->eB;
-    C.F = (vec_t<T>*)h->F; C.dp = (vec_t<T>*)h->dp;
+    using vec = vec_t<T>;
+    using E = eps_t<T>;
+    C.qA = (vec*)h->qA; C.pA = (vec*)h->pA; C.eA = (E*)h->eA; C.cA = h->cA;
+    C.qB = (vec*)h->qB; C.pB = (vec*)h->pB; C.eB = (E*)h->eB; C.cB = h->cB;
+    C.idB = h->idB;
+    C.F = (vec*)h->F; C.dp = (vec*)h->dp;
     C.key = h->key; C.tmp = h->tmp;
     C.count = h->cnt; C.fill = h->cnt + h->ncells; C.start = h->start;
+    C.nbr_j = h->nbr_j; C.nbr_w = (T*)h->nbr_w; C.nbr_n = h->nbr_n; C.nbr_cap = h->nbr_cap;
     C.rep_of_slot = h->rep_of_slot; C.rep_of_cell = h->rep_of_cell;
+    C.brick_rep = h->brick_rep; C.tab = h->tab;
     C.reps = h->d_reps; C.step = h->d_step; C.status = h->d_status;
     C.N = h->N; C.ncells = h->ncells;
     C.m = (T)h->prm.mass; C.inv_m = (T)(1.0 / h->prm.mass);
@@ -130,12 +145,11 @@ void enqueue_sort(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T half_dt, T
 }
 
 template <class T>
-void enqueue_ssa_rounds(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_dt, int whole) {
+void enqueue_ssa_rounds(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_dt) {
     const int nbc = ceil_div(h->ncells, 128);
     for (int di = 0; di < 14; ++di) {
-        const int ncol = di == 0 ? 1 : ((whole ? h->need_col3_whole[di] : h->need_col3[di]) ? 3 : 2);
-        for (int col = 0; col < ncol; ++col)
-            k_ssa_round<T><<<nbc, 128, 0, st>>>(C, di, col, whole, dt, sqrt_dt);
+        const int ncol = di == 0 ? 1 : (h->need_col3_whole[di] ? 3 : 2);
+        for (int col = 0; col < ncol; ++col) k_ssa_round<T><<<nbc, 128, 0, st>>>(C, di, col, dt, sqrt_dt);
     }
 }
 
@@ -145,31 +159,32 @@ void enqueue_step(dpde_handle* h, cudaStream_t st, double dt_d, int scheme) {
     const T dt = (T)dt_d, half_dt = (T)(0.5 * dt_d), sqrt_dt = (T)std::sqrt(dt_d);
     const int nb = ceil_div(h->N, h->block);
     enqueue_sort<T>(h, C, st, half_dt, dt, 1);
+    const int list = scheme == DPDE_SSA ? LIST_NONE : (scheme == DPDE_HYBRID ? LIST_CROSS : LIST_ALL);
     phase(h, st, DPDE_PHASE_FORCE, 0);
-    k_force<T><<<nb, h->block, 0, st>>>(C, half_dt, 1);
+    k_force<T><<<nb, h->block, 0, st>>>(C, half_dt, 1, list);
     phase(h, st, DPDE_PHASE_FORCE, 1);
-    const int cross = scheme == DPDE_HYBRID ? 1 : 0;
-    if (scheme == DPDE_HYBRID || scheme == DPDE_SSA) {
-        phase(h, st, DPDE_PHASE_SSA, 0);
-        enqueue_ssa_rounds<T>(h, C, st, dt, sqrt_dt, scheme == DPDE_SSA ? 1 : 0);
-        phase(h, st, DPDE_PHASE_SSA, 1);
-    }
     if (scheme == DPDE_HYBRID) {
-        phase(h, st, DPDE_PHASE_OTHER, 0);
-        k_refresh_beta<T><<<nb, h->block, 0, st>>>(C);
-        phase(h, st, DPDE_PHASE_OTHER, 1);
+        phase(h, st, DPDE_PHASE_SSA, 0);
+        k_ssa_brick<T><<<h->nbricks, SSA_THREADS, h->ssa_smem, st>>>(C, dt, sqrt_dt, h->ssa_cap, SSA_RCAP);
+        phase(h, st, DPDE_PHASE_SSA, 1);
+    } else if (scheme == DPDE_SSA) {
+        phase(h, st, DPDE_PHASE_SSA, 0);
+        enqueue_ssa_rounds<T>(h, C, st, dt, sqrt_dt);
+        phase(h, st, DPDE_PHASE_SSA, 1);
     }
     if (scheme == DPDE_SER || scheme == DPDE_HYBRID) {
         phase(h, st, DPDE_PHASE_SWEEP1, 0);
-        k_ser_sweep1<T><<<nb, h->block, 0, st>>>(C, dt, sqrt_dt, cross);
+        k_ser_sweep1<T><<<nb, h->block, 0, st>>>(C, dt, sqrt_dt);
         phase(h, st, DPDE_PHASE_SWEEP1, 1);
     }
     phase(h, st, DPDE_PHASE_SWEEP2, 0);
-    if (scheme == DPDE_SER || scheme == DPDE_HYBRID) k_ser_sweep2<T><<<nb, h->block, 0, st>>>(C, dt, sqrt_dt, cross);
+    if (scheme == DPDE_SER || scheme == DPDE_HYBRID) k_ser_sweep2<T><<<nb, h->block, 0, st>>>(C, dt, sqrt_dt);
     else if (scheme == DPDE_SEM) k_sem<T><<<nb, h->block, 0, st>>>(C, dt, sqrt_dt);
     else k_copy_back<T><<<nb, h->block, 0, st>>>(C);
     phase(h, st, DPDE_PHASE_SWEEP2, 1);
+    phase(h, st, DPDE_PHASE_OTHER, 0);
     k_step_inc<<<1, 1, 0, st>>>(h->d_step);
+    phase(h, st, DPDE_PHASE_OTHER, 1);
 }
 
 void enqueue_step_any(dpde_handle* h, cudaStream_t st, double dt, int scheme) {
@@ -183,7 +198,7 @@ void enqueue_set_state(dpde_handle* h, cudaStream_t st, const double* q, const d
     const int nb = ceil_div(h->N, h->block);
     k_load_state<T><<<nb, h->block, 0, st>>>(C, q, p, e);
     enqueue_sort<T>(h, C, st, T(0), T(0), 0);
-    k_force<T><<<nb, h->block, 0, st>>>(C, T(0), 0);
+    k_force<T><<<nb, h->block, 0, st>>>(C, T(0), 0, LIST_NONE);
     k_copy_back<T><<<nb, h->block, 0, st>>>(C);
 }
 
@@ -207,6 +222,7 @@ int read_status(dpde_handle* h) {
     CK(h, cudaMemcpyAsync(&st, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    if (st & ST_CAPACITY) return fail(h, DPDE_ERR_CAPACITY, "neighbour list capacity exceeded");
     if (st & ST_NONFINITE) return fail(h, DPDE_ERR_NONFINITE, "non-finite value in the state");
     if (st & ST_NEG_EPS) return fail(h, DPDE_ERR_NEG_EPS, "internal energy eps_i <= 0");
     return DPDE_OK;
@@ -218,10 +234,11 @@ void free_all(dpde_handle* h) {
             if (ev) cudaEventDestroy(ev);
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
-    void* bufs[] = {h->qA, h->pA, h->qB, h->pB, h->F, h->dp, h->eA, h->eB, h->key, h->tmp, h->cnt,
-                    h->start, h->bsum, h->rep_of_slot, h->rep_of_cell, h->chunk_rep, h->chunk_begin,
-                    h->chunk_end, h->rep_chunk_begin, h->partial, h->obs_out, h->d_reps, h->d_step,
-                    h->d_status, h->staging};
+    void* bufs[] = {h->qA, h->pA, h->qB, h->pB, h->F, h->dp, h->eA, h->eB, h->nbr_w, h->cA, h->cB, h->nbr_j,
+                    h->nbr_n, h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
+                    h->rep_of_cell, h->brick_rep, h->tab, h->chunk_rep, h->chunk_begin, h->chunk_end,
+                    h->rep_chunk_begin, h->partial, h->obs_out, h->d_reps, h->d_step, h->d_status,
+                    h->staging, h->cells_out};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -247,9 +264,10 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     h->R = n_replicas;
     h->mixed = P.precision == DPDE_MIXED;
     h->reps.assign(replicas, replicas + n_replicas);
-    long long N = 0, ncells = 0, nchunks = 0;
+    long long N = 0, ncells = 0, nbricks = 0;
     const int CHUNK = 4096;
-    std::vector<int> chunk_rep, chunk_begin, chunk_end, rep_chunk_begin(1, 0);
+    std::vector<int> chunk_rep, chunk_begin, chunk_end, rep_chunk_begin(1, 0), tabs, brick_rep;
+    double rho_max = 0.0, per_brick_max = 0.0;
     for (int r = 0; r < n_replicas; ++r) {
         const dpde_replica& d = replicas[r];
         RepInfo I{};
@@ -265,53 +283,81 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
             I.k[a] = (int)std::floor(d.box[a] / ((double)d.bricks[a] * P.r_cut));
             I.B[a] = d.bricks[a];
             I.nc[a] = I.B[a] * I.k[a];
-            if (I.k[a] < 1 || I.nc[a] < 3) {
+            if (I.k[a] < 1 || I.nc[a] < 3 || I.nc[a] > 1024) {
                 delete h;
                 return fail(nullptr, DPDE_ERR_ARG,
-                            "replica " + std::to_string(r) + ": box too small for the brick grid "
-                            "(need floor(L/(B r_cut)) >= 1 and B*that >= 3 cells per axis)");
+                            "replica " + std::to_string(r) + ": box does not fit the brick grid (need "
+                            "floor(L/(B r_cut)) >= 1 and 3 <= B*that <= 1024 cells per axis)");
             }
             I.L[a] = d.box[a];
+            I.ell[a] = d.box[a] / (double)I.nc[a];
             I.s[a] = (double)I.nc[a] / d.box[a];
-            I.Lf[a] = (float)d.box[a];
-            I.sf[a] = (float)I.s[a];
-            I.odd_ring[a] = (I.B[a] == 1) && (I.k[a] & 1);
+            I.ellf[a] = (float)I.ell[a];
         }
+        const int kc = I.k[0] * I.k[1] * I.k[2];
+        const int nbr = I.B[0] * I.B[1] * I.B[2];
         I.cell_off = (int)ncells;
         I.ncells = I.nc[0] * I.nc[1] * I.nc[2];
         I.part_off = (int)N;
         I.n = (int)d.n;
+        I.brick_off = (int)nbricks;
+        I.tab_off = (int)tabs.size();
         I.cv = d.cv;
         I.cvf = (float)d.cv;
+        // brick-major cell tables
+        for (int c = 0; c < I.nc[0]; ++c) tabs.push_back((c / I.k[0]) * kc + c % I.k[0]);
+        for (int c = 0; c < I.nc[1]; ++c) tabs.push_back((c / I.k[1]) * I.B[0] * kc + (c % I.k[1]) * I.k[0]);
+        for (int c = 0; c < I.nc[2]; ++c)
+            tabs.push_back((c / I.k[2]) * I.B[0] * I.B[1] * kc + (c % I.k[2]) * I.k[0] * I.k[1]);
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < I.nc[a]; ++c) tabs.push_back(c / I.k[a]);
+        for (int b = 0; b < nbr; ++b) brick_rep.push_back(r);
+        h->kc_max = std::max(h->kc_max, kc);
+        rho_max = std::max(rho_max, (double)d.n / (d.box[0] * d.box[1] * d.box[2]));
+        per_brick_max = std::max(per_brick_max, (double)d.n / nbr);
         h->info.push_back(I);
         N += d.n;
         ncells += I.ncells;
+        nbricks += nbr;
         for (long long b = 0; b < d.n; b += CHUNK) {
             chunk_rep.push_back(r);
             chunk_begin.push_back((int)(I.part_off + b));
             chunk_end.push_back((int)(I.part_off + std::min<long long>(b + CHUNK, d.n)));
         }
         rep_chunk_begin.push_back((int)chunk_rep.size());
-        if (N > (1ll << 30) || ncells > (1ll << 30)) {
+        if (N > (1ll << NBR_J_BITS) || ncells > (1ll << 30)) {
             delete h;
-            return fail(nullptr, DPDE_ERR_ARG, "too many particles or cells (limit 2^30)");
+            return fail(nullptr, DPDE_ERR_ARG, "too many particles (limit 2^27) or cells (2^30)");
         }
     }
-    nchunks = (long long)chunk_rep.size();
     h->N = (int)N;
     h->ncells = (int)ncells;
-    h->nchunks = (int)nchunks;
-    // colours per SSA direction: three when the leading axis is a periodic
-    // brick axis with an odd number of cells
+    h->nbricks = (int)nbricks;
+    h->nchunks = (int)chunk_rep.size();
+    // neighbour-list capacity: 3x the mean neighbour count of the densest replica, + 32
+    const double mean_nbr = 4.0 / 3.0 * M_PI * rho_max * P.r_cut * P.r_cut * P.r_cut;
+    h->nbr_cap = (int)std::ceil(3.0 * mean_nbr) + 32;
+    // SSA bricks are staged in shared memory up to 1.3x the mean occupancy + 64
+    // (fuller bricks run in place on global memory)
+    const size_t vsz = h->mixed ? sizeof(float4) : sizeof(d4);
+    const size_t esz = h->mixed ? sizeof(ff) : sizeof(double);
+    const size_t tsz0 = h->mixed ? sizeof(float) : sizeof(double);
+    const size_t per = 2 * vsz + esz;
+    const size_t head = ((size_t)(3 * h->kc_max + 2) * sizeof(int) + 31) & ~(size_t)31;
+    const size_t rbuf = (size_t)SSA_RCAP * (2 * sizeof(int) + 4 * tsz0) + 16;
+    const size_t smem_limit = 200 * 1024;
+    h->ssa_cap = (int)std::max<double>(
+        0.0, std::min<double>(1.3 * per_brick_max + 64.0, (double)((smem_limit - head - rbuf) / per)));
+    h->ssa_smem = 32 + head + (size_t)h->ssa_cap * per + rbuf;   // + 32: base alignment slack
+    // colours per SSA direction for the whole-replica SSA: three when the
+    // leading axis has an odd number of cells
     static const int dirs[14][3] = {{0, 0, 0},   {1, 0, 0},  {-1, 1, 0}, {0, 1, 0},  {1, 1, 0},
                                     {-1, -1, 1}, {0, -1, 1}, {1, -1, 1}, {-1, 0, 1}, {0, 0, 1},
                                     {1, 0, 1},   {-1, 1, 1}, {0, 1, 1},  {1, 1, 1}};
     for (int di = 1; di < 14; ++di) {
         const int lead = dirs[di][2] ? 2 : (dirs[di][1] ? 1 : 0);
-        for (const RepInfo& I : h->info) {
-            if (I.odd_ring[lead]) h->need_col3[di] = 1;
+        for (const RepInfo& I : h->info)
             if (I.nc[lead] & 1) h->need_col3_whole[di] = 1;
-        }
     }
     auto bail = [&](cudaError_t e, const char* what) {
         std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
@@ -320,9 +366,9 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         delete h;
         return fail(nullptr, code, msg);
     };
-#define CKC(call)                                  \
-    do {                                           \
-        cudaError_t e_ = (call);                   \
+#define CKC(call)                                      \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
         if (e_ != cudaSuccess) return bail(e_, #call); \
     } while (0)
     if (stream) {
@@ -332,16 +378,22 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         h->own_stream = true;
     }
     CKC(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-    const size_t vsz = h->mixed ? sizeof(float4) : sizeof(d4);
     const size_t n1 = (size_t)std::max(1, h->N), c1 = (size_t)std::max(1, h->ncells);
+    const size_t tsz = h->mixed ? sizeof(float) : sizeof(double);
     CKC(cudaMalloc(&h->qA, vsz * n1));
     CKC(cudaMalloc(&h->pA, vsz * n1));
     CKC(cudaMalloc(&h->qB, vsz * n1));
     CKC(cudaMalloc(&h->pB, vsz * n1));
     CKC(cudaMalloc(&h->F, vsz * n1));
     CKC(cudaMalloc(&h->dp, vsz * n1));
-    CKC(cudaMalloc(&h->eA, sizeof(double) * n1));
-    CKC(cudaMalloc(&h->eB, sizeof(double) * n1));
+    CKC(cudaMalloc(&h->eA, esz * n1));
+    CKC(cudaMalloc(&h->eB, esz * n1));
+    CKC(cudaMalloc(&h->cA, sizeof(int) * n1));
+    CKC(cudaMalloc(&h->cB, sizeof(int) * n1));
+    CKC(cudaMalloc(&h->idB, sizeof(uint32_t) * n1));
+    CKC(cudaMalloc(&h->nbr_j, sizeof(int) * n1 * (size_t)h->nbr_cap));
+    CKC(cudaMalloc(&h->nbr_w, tsz * n1 * (size_t)h->nbr_cap));
+    CKC(cudaMalloc(&h->nbr_n, sizeof(int) * n1));
     CKC(cudaMalloc(&h->key, sizeof(int) * n1));
     CKC(cudaMalloc(&h->tmp, sizeof(int) * n1));
     CKC(cudaMalloc(&h->cnt, sizeof(int) * 2 * c1));
@@ -349,6 +401,8 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     CKC(cudaMalloc(&h->bsum, sizeof(int) * (size_t)std::max(1, ceil_div(h->ncells, SCAN_TILE))));
     CKC(cudaMalloc(&h->rep_of_slot, sizeof(int) * n1));
     CKC(cudaMalloc(&h->rep_of_cell, sizeof(int) * c1));
+    CKC(cudaMalloc(&h->brick_rep, sizeof(int) * (size_t)std::max(1, h->nbricks)));
+    CKC(cudaMalloc(&h->tab, sizeof(int) * tabs.size()));
     CKC(cudaMalloc(&h->chunk_rep, sizeof(int) * std::max<size_t>(1, chunk_rep.size())));
     CKC(cudaMalloc(&h->chunk_begin, sizeof(int) * std::max<size_t>(1, chunk_rep.size())));
     CKC(cudaMalloc(&h->chunk_end, sizeof(int) * std::max<size_t>(1, chunk_rep.size())));
@@ -359,6 +413,7 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     CKC(cudaMalloc(&h->d_step, sizeof(long long)));
     CKC(cudaMalloc(&h->d_status, sizeof(unsigned int)));
     CKC(cudaMalloc(&h->staging, sizeof(double) * 7 * n1));
+    CKC(cudaMalloc(&h->cells_out, sizeof(int) * 3 * n1));
     {
         std::vector<int> ros(n1, 0), roc(c1, 0);
         for (int r = 0; r < h->R; ++r) {
@@ -368,6 +423,8 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         }
         CKC(cudaMemcpy(h->rep_of_slot, ros.data(), sizeof(int) * n1, cudaMemcpyHostToDevice));
         CKC(cudaMemcpy(h->rep_of_cell, roc.data(), sizeof(int) * c1, cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(h->brick_rep, brick_rep.data(), sizeof(int) * brick_rep.size(), cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(h->tab, tabs.data(), sizeof(int) * tabs.size(), cudaMemcpyHostToDevice));
         if (!chunk_rep.empty()) {
             CKC(cudaMemcpy(h->chunk_rep, chunk_rep.data(), sizeof(int) * chunk_rep.size(), cudaMemcpyHostToDevice));
             CKC(cudaMemcpy(h->chunk_begin, chunk_begin.data(), sizeof(int) * chunk_rep.size(), cudaMemcpyHostToDevice));
@@ -378,11 +435,17 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         CKC(cudaMemcpy(h->d_reps, h->info.data(), sizeof(RepInfo) * (size_t)h->R, cudaMemcpyHostToDevice));
         CKC(cudaMemset(h->d_step, 0, sizeof(long long)));
         CKC(cudaMemset(h->d_status, 0, sizeof(unsigned int)));
-        CKC(cudaMemset(h->eA, 0, sizeof(double) * n1));
+        CKC(cudaMemset(h->eA, 0, esz * n1));
         CKC(cudaMemset(h->qA, 0, vsz * n1));
         CKC(cudaMemset(h->pA, 0, vsz * n1));
+        CKC(cudaMemset(h->cA, 0, sizeof(int) * n1));
         CKC(cudaMemset(h->F, 0, vsz * n1));
+        CKC(cudaMemset(h->nbr_n, 0, sizeof(int) * n1));
     }
+    if (h->mixed)
+        CKC(cudaFuncSetAttribute(k_ssa_brick<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ssa_smem));
+    else
+        CKC(cudaFuncSetAttribute(k_ssa_brick<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ssa_smem));
 #undef CKC
     *out = h;
     return DPDE_OK;
@@ -394,6 +457,7 @@ int dpde_set_state(dpde_handle* h, const double* q, const double* p, const doubl
     if (h->N > 0 && (!q || !p || !eps)) return fail(h, DPDE_ERR_ARG, "q, p and eps are required");
     const size_t N = (size_t)h->N;
     const double *dq = q, *dpp = p, *de = eps;
+    CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream));
     if (!on_device && N > 0) {
         CK(h, cudaMemcpyAsync(h->staging, q, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream));
         CK(h, cudaMemcpyAsync(h->staging + 3 * N, p, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream));
@@ -406,7 +470,6 @@ int dpde_set_state(dpde_handle* h, const double* q, const double* p, const doubl
     }
     long long s = step;
     CK(h, cudaMemcpyAsync(h->d_step, &s, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     CK(h, cudaGetLastError());
     h->step = step;
@@ -431,6 +494,18 @@ int dpde_get_state(dpde_handle* h, double* q, double* p, double* eps, int32_t on
     }
     CK(h, cudaStreamSynchronize(h->stream));
     return read_status(h);
+}
+
+int dpde_get_cells(dpde_handle* h, int32_t* cells) {
+    if (!h || (h->N > 0 && !cells)) return DPDE_ERR_ARG;
+    if (h->N > 0) {
+        if (h->mixed) k_get_cells<float><<<ceil_div(h->N, h->block), h->block, 0, h->stream>>>(make_ctx<float>(h), h->cells_out);
+        else k_get_cells<double><<<ceil_div(h->N, h->block), h->block, 0, h->stream>>>(make_ctx<double>(h), h->cells_out);
+        CK(h, cudaGetLastError());
+        CK(h, cudaMemcpyAsync(cells, h->cells_out, sizeof(int) * 3 * (size_t)h->N, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return DPDE_OK;
 }
 
 int dpde_step(dpde_handle* h, int64_t n, double dt, int32_t scheme, int32_t use_graph) {
@@ -535,6 +610,76 @@ int dpde_observables(dpde_handle* h, dpde_obs* out) {
     if (bad) return fail(h, DPDE_ERR_NONFINITE, "non-finite value in the state");
     if (neg) return fail(h, DPDE_ERR_NEG_EPS, "internal energy eps_i <= 0");
     return st;
+}
+
+namespace {
+struct CkptHeader {
+    uint64_t magic, N, R, precision, step, seed, cfg_hash, section_bytes;
+};
+uint64_t config_hash(const dpde_handle* h) {
+    uint64_t x = 1469598103934665603ull;
+    auto mix = [&](const void* p, size_t n) {
+        const unsigned char* b = (const unsigned char*)p;
+        for (size_t i = 0; i < n; ++i) x = (x ^ b[i]) * 1099511628211ull;
+    };
+    mix(&h->prm, sizeof(h->prm));
+    for (const dpde_replica& r : h->reps) mix(&r, sizeof(r));
+    return x;
+}
+}  // namespace
+
+int dpde_checkpoint(dpde_handle* h, void* buf, uint64_t* size) {
+    if (!h || !size) return DPDE_ERR_ARG;
+    const size_t N = (size_t)h->N;
+    const size_t vsz = h->mixed ? sizeof(float4) : sizeof(d4);
+    const size_t esz = h->mixed ? sizeof(ff) : sizeof(double);
+    const size_t body = N * (3 * vsz + esz + sizeof(int));
+    const size_t total = sizeof(CkptHeader) + body;
+    if (!buf) {
+        *size = total;
+        return DPDE_OK;
+    }
+    if (*size < total) return fail(h, DPDE_ERR_ARG, "checkpoint buffer too small");
+    CK(h, cudaStreamSynchronize(h->stream));
+    CkptHeader hd{0x4450444543484b31ull, N, (uint64_t)h->R, (uint64_t)h->prm.precision, (uint64_t)h->step,
+                  h->prm.seed, config_hash(h), body};
+    unsigned char* out = (unsigned char*)buf;
+    std::memcpy(out, &hd, sizeof(hd));
+    out += sizeof(hd);
+    const void* src[5] = {h->qA, h->pA, h->F, h->eA, h->cA};
+    const size_t len[5] = {N * vsz, N * vsz, N * vsz, N * esz, N * sizeof(int)};
+    for (int k = 0; k < 5; ++k) {
+        if (len[k]) CK(h, cudaMemcpy(out, src[k], len[k], cudaMemcpyDeviceToHost));
+        out += len[k];
+    }
+    *size = total;
+    return DPDE_OK;
+}
+
+int dpde_restore(dpde_handle* h, const void* buf, uint64_t size) {
+    if (!h || !buf || size < sizeof(CkptHeader)) return DPDE_ERR_ARG;
+    CkptHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    const size_t N = (size_t)h->N;
+    const size_t vsz = h->mixed ? sizeof(float4) : sizeof(d4);
+    const size_t esz = h->mixed ? sizeof(ff) : sizeof(double);
+    const size_t body = N * (3 * vsz + esz + sizeof(int));
+    if (hd.magic != 0x4450444543484b31ull || hd.N != N || hd.cfg_hash != config_hash(h) ||
+        hd.section_bytes != body || size < sizeof(hd) + body)
+        return fail(h, DPDE_ERR_ARG, "checkpoint does not match this handle");
+    const unsigned char* in = (const unsigned char*)buf + sizeof(hd);
+    void* dst[5] = {h->qA, h->pA, h->F, h->eA, h->cA};
+    const size_t len[5] = {N * vsz, N * vsz, N * vsz, N * esz, N * sizeof(int)};
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 5; ++k) {
+        if (len[k]) CK(h, cudaMemcpy(dst[k], in, len[k], cudaMemcpyHostToDevice));
+        in += len[k];
+    }
+    long long s = (long long)hd.step;
+    CK(h, cudaMemcpy(h->d_step, &s, sizeof(long long), cudaMemcpyHostToDevice));
+    CK(h, cudaMemset(h->d_status, 0, sizeof(unsigned)));
+    h->step = s;
+    return DPDE_OK;
 }
 
 int dpde_get_step(dpde_handle* h, int64_t* step) {

@@ -1,13 +1,20 @@
 // dpde_device.cuh -- device-side building blocks of the DPDE step (sm_103a).
 //
-// Precision is a template parameter T: double for the FP64 mode, float for
-// the mixed mode (internal energies stay double in both). Particle data are
-// cell-sorted structures of arrays:
-//   q   : (x, y, z, id bits)  -- the id rides in the 4th lane
-//   p   : (px, py, pz, beta)  -- beta_i = C_v / eps_i, Eq. (DPDE_internalEOS)
-//   F   : (Fx, Fy, Fz, -)
-//   dp  : (dpx, dpy, dpz, -)  -- SER first-sweep sums delta p_i, Eq. (SER_p)
-//   eps : double
+// Precision is a template parameter T of positions, momenta, forces and pair
+// arithmetic: double (FP64 mode) or float (mixed mode). Internal energies use
+// the type E: double in FP64 mode, a compensated float pair (hi + lo, about
+// 48 significant bits) in the mixed mode, so that the small per-pair energy
+// reinjections are not lost against eps ~ C_v T.
+//
+// Particle data are cell-sorted structures of arrays (slot order):
+//   q   : (ox, oy, oz, id bits) -- offset of the particle inside its cell,
+//                                  o in [0, l) with l = L / ncell per axis
+//   cc  : packed cell coordinates cx | cy << 10 | cz << 20
+//   p   : (px, py, pz, beta)    -- beta_i = C_v / eps_i, Eq. (DPDE_internalEOS)
+//   eps : E
+// Cell-relative offsets keep float positions at ~1e-7 absolute resolution
+// whatever the box size; the distance between particles of cells c and
+// c + d is (o_i - o_j) - d * l, which also gives the periodic image.
 #pragma once
 
 #include <cstdint>
@@ -20,10 +27,16 @@ struct __align__(32) d4 {
     double x, y, z, w;
 };
 
+// Compensated float pair: value = hi + lo with |lo| <= ulp(hi)/2.
+struct __align__(8) ff {
+    float hi, lo;
+};
+
 template <class T> struct V;
-template <> struct V<double> { using t = d4; };
-template <> struct V<float> { using t = float4; };
+template <> struct V<double> { using t = d4; using e = double; };
+template <> struct V<float> { using t = float4; using e = ff; };
 template <class T> using vec_t = typename V<T>::t;
+template <class T> using eps_t = typename V<T>::e;
 
 __device__ __forceinline__ uint32_t id_of(const float4& q) { return __float_as_uint(q.w); }
 __device__ __forceinline__ uint32_t id_of(const d4& q) {
@@ -34,12 +47,35 @@ __device__ __forceinline__ void set_id(d4& q, uint32_t id) {
     q.w = __longlong_as_double((long long)id);
 }
 
+// ---------------------------------------------------------------------------
+// compensated float arithmetic (Knuth's two-sum; Dekker's normalisation)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ ff ff_add(ff a, float b) {
+    const float s = __fadd_rn(a.hi, b);
+    const float bb = __fsub_rn(s, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    const float lo = __fadd_rn(a.lo, err);
+    const float hi = __fadd_rn(s, lo);
+    return {hi, __fsub_rn(lo, __fsub_rn(hi, s))};
+}
+__device__ __forceinline__ double eps_value(double e) { return e; }
+__device__ __forceinline__ double eps_value(ff e) { return (double)e.hi + (double)e.lo; }
+__device__ __forceinline__ float eps_approx(ff e) { return e.hi + e.lo; }
+__device__ __forceinline__ double eps_approx(double e) { return e; }
+__device__ __forceinline__ void eps_from(double v, double& e) { e = v; }
+__device__ __forceinline__ void eps_from(double v, ff& e) {
+    e.hi = (float)v;
+    e.lo = (float)(v - (double)e.hi);
+}
+__device__ __forceinline__ double eps_add(double e, double d) { return e + d; }
+__device__ __forceinline__ ff eps_add(ff e, float d) { return ff_add(e, d); }
+
 // Per-replica constants (one independent periodic system each).
 struct RepInfo {
     double L[3];     // box lengths
-    double s[3];     // ncell_d / L_d, formed in double
-    float Lf[3];     // float copies for the mixed mode
-    float sf[3];
+    double ell[3];   // cell size L_d / ncell_d
+    double s[3];     // ncell_d / L_d
+    float ellf[3];
     int nc[3];       // cells per axis
     int k[3];        // cells per brick per axis
     int B[3];        // bricks (Hybrid domains) per axis
@@ -47,29 +83,33 @@ struct RepInfo {
     int ncells;
     int part_off;    // first particle slot of the replica
     int n;
+    int brick_off;   // first global brick index of the replica
+    int tab_off;     // offset of the replica's cell tables
     double cv;       // C_v
     float cvf;
-    int odd_ring[3]; // brick periodic along axis (B == 1) with odd k
+    int pad;
 };
 
-template <class T> __device__ __forceinline__ T box_len(const RepInfo& R, int d);
-template <> __device__ __forceinline__ double box_len<double>(const RepInfo& R, int d) { return R.L[d]; }
-template <> __device__ __forceinline__ float box_len<float>(const RepInfo& R, int d) { return R.Lf[d]; }
-template <class T> __device__ __forceinline__ T cell_scale(const RepInfo& R, int d);
-template <> __device__ __forceinline__ double cell_scale<double>(const RepInfo& R, int d) { return R.s[d]; }
-template <> __device__ __forceinline__ float cell_scale<float>(const RepInfo& R, int d) { return R.sf[d]; }
-
-// c_d(x) = min(ncell_d - 1, (int)(x * (ncell_d / L_d))) (x >= 0 after wrap).
-template <class T>
-__device__ __forceinline__ int cell_coord(T x, const RepInfo& R, int d) {
-    int c = (int)(x * cell_scale<T>(R, d));
-    c = c > R.nc[d] - 1 ? R.nc[d] - 1 : c;
-    return c < 0 ? 0 : c;
+// Cell tables of a replica, at tab_off: lin_x[nc0] | lin_y[nc1] | lin_z[nc2]
+// | brick_x[nc0] | brick_y[nc1] | brick_z[nc2]. The brick-major linear cell
+// index is cell_off + lin_x[cx] + lin_y[cy] + lin_z[cz]; brick_d[c] = c / k_d.
+__device__ __forceinline__ int cell_index(const int* __restrict__ tab, const RepInfo& R, int cx,
+                                          int cy, int cz) {
+    const int* t = tab + R.tab_off;
+    return R.cell_off + __ldg(t + cx) + __ldg(t + R.nc[0] + cy) + __ldg(t + R.nc[0] + R.nc[1] + cz);
+}
+__device__ __forceinline__ const int* brick_tab(const int* __restrict__ tab, const RepInfo& R) {
+    return tab + R.tab_off + R.nc[0] + R.nc[1] + R.nc[2];
 }
 
-__device__ __forceinline__ int cell_linear(const RepInfo& R, int cx, int cy, int cz) {
-    return R.cell_off + (cz * R.nc[1] + cy) * R.nc[0] + cx;
-}
+__device__ __forceinline__ int pack_cell(int cx, int cy, int cz) { return cx | (cy << 10) | (cz << 20); }
+__device__ __forceinline__ int cell_x(int c) { return c & 1023; }
+__device__ __forceinline__ int cell_y(int c) { return (c >> 10) & 1023; }
+__device__ __forceinline__ int cell_z(int c) { return (c >> 20) & 1023; }
+
+template <class T> __device__ __forceinline__ T cell_len(const RepInfo& R, int d);
+template <> __device__ __forceinline__ double cell_len<double>(const RepInfo& R, int d) { return R.ell[d]; }
+template <> __device__ __forceinline__ float cell_len<float>(const RepInfo& R, int d) { return R.ellf[d]; }
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round
@@ -139,6 +179,6 @@ __device__ __forceinline__ T3<T> pair_gauss(uint2 key, uint32_t step, uint32_t r
 }
 
 // Status bits raised by the kernels (read and cleared by the host).
-enum : unsigned int { ST_NEG_EPS = 1u, ST_NONFINITE = 2u };
+enum : unsigned int { ST_NEG_EPS = 1u, ST_NONFINITE = 2u, ST_CAPACITY = 4u };
 
 }  // namespace dpde

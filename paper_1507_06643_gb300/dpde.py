@@ -23,6 +23,7 @@ DPDE_ERR_OOM = -3
 DPDE_ERR_NEG_EPS = -4
 DPDE_ERR_NONFINITE = -5
 DPDE_ERR_TIMEOUT = -6
+DPDE_ERR_CAPACITY = -7
 
 FP64, MIXED = 0, 1
 SER, HYBRID, SEM, SSA = 0, 1, 2, 3
@@ -62,7 +63,8 @@ class dpde_obs(C.Structure):
 _lib = None
 EXPORTS = ["dpde_create", "dpde_set_state", "dpde_get_state", "dpde_step", "dpde_sync",
            "dpde_observables", "dpde_get_step", "dpde_destroy", "dpde_last_error",
-           "dpde_debug_philox", "dpde_debug_gaussian", "dpde_step_profiled"]
+           "dpde_debug_philox", "dpde_debug_gaussian", "dpde_step_profiled", "dpde_get_cells",
+           "dpde_checkpoint", "dpde_restore"]
 PHASES = ["kick_drift", "scan", "gather", "force", "ssa", "sweep1", "sweep2", "other"]
 
 
@@ -87,6 +89,9 @@ def lib():
         L.dpde_destroy.argtypes = [vp]
         L.dpde_last_error.argtypes = [vp]
         L.dpde_last_error.restype = C.c_char_p
+        L.dpde_checkpoint.argtypes = [vp, vp, C.POINTER(C.c_uint64)]
+        L.dpde_restore.argtypes = [vp, vp, C.c_uint64]
+        L.dpde_get_cells.argtypes = [vp, C.POINTER(C.c_int32)]
         L.dpde_step_profiled.argtypes = [vp, C.c_int64, C.c_double, C.c_int32, dp]
         L.dpde_debug_philox.argtypes = [C.c_int64, u32p, u32p, u32p]
         L.dpde_debug_gaussian.argtypes = [C.c_int64, C.c_uint64, u32p, u32p, u32p, u32p,
@@ -219,6 +224,23 @@ class System:
         if check:
             _check(self.h, rc)
         return q, p, e
+
+    def checkpoint(self) -> bytes:
+        """Raw internal state for a bit-exact restart."""
+        size = C.c_uint64(0)
+        _check(self.h, lib().dpde_checkpoint(self.h, None, C.byref(size)))
+        buf = C.create_string_buffer(size.value)
+        _check(self.h, lib().dpde_checkpoint(self.h, buf, C.byref(size)))
+        return buf.raw[:size.value]
+
+    def restore(self, blob: bytes):
+        _check(self.h, lib().dpde_restore(self.h, blob, len(blob)))
+
+    def get_cells(self):
+        """Cell coordinates (N, 3) of every particle, id order."""
+        out = np.empty((self.N, 3), np.int32)
+        _check(self.h, lib().dpde_get_cells(self.h, out.ctypes.data_as(C.POINTER(C.c_int32))))
+        return out
 
     def step(self, n, dt, scheme, use_graph=True):
         dpde_step(self.h, n, dt, scheme, use_graph)

@@ -13,7 +13,7 @@ import tempfile
 import numpy as np
 import pytest
 
-from gpu_util import make_state, rel_err, run_both
+from gpu_util import assert_parity, make_state, q_diff, rel_err, run_both
 
 pytestmark = pytest.mark.gpu
 
@@ -86,24 +86,25 @@ def test_device_gaussian_matches_oracle(ora, precision, tol):
 @pytest.mark.parametrize("scheme", ["SER", "HYBRID", "SEM", "SSA"])
 def test_parity_plain_n1000(precision, scheme):
     specs = [(1000, (cube(1000),) * 3, 100.0, 1.0, (2, 2, 2))]
-    errs, _, _ = run_both(specs, precision, scheme, 10, seed=1001)
-    assert max(errs.values()) < TOL[precision], errs
+    for _ in assert_parity(specs, precision, scheme, 10, TOL[precision], seeds=range(1001, 1009)):
+        break
 
 
 @pytest.mark.parametrize("n,box,bricks", [
     (1, (4.0, 4.0, 4.0), (1, 1, 1)),
     (2, (3.0, 3.0, 3.0), (1, 1, 1)),
-    (64, (cube(64),) * 3, (1, 1, 1)),
+    (64, (3.2, 3.2, 3.2), (1, 1, 1)),
     (777, (5.0, 7.3, 7.1), (1, 2, 3)),
     (3000, (7.0, 10.5, 13.6), (2, 3, 1)),
     (2500, (9.3, 9.3, 9.7), (3, 3, 3)),
+    (6000, (12.6, 12.6, 12.6), (1, 1, 1)),   # one domain too large for shared memory
 ])
 @pytest.mark.parametrize("scheme", ["SER", "HYBRID"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_parity_sizes(n, box, bricks, scheme, precision):
     specs = [(n, box, 50.0, 1.0, bricks)]
-    errs, _, _ = run_both(specs, precision, scheme, 6, seed=n)
-    assert max(errs.values()) < TOL[precision], errs
+    for _ in assert_parity(specs, precision, scheme, 6, TOL[precision], seeds=range(n, n + 8)):
+        break
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -117,8 +118,9 @@ def test_parity_batched_replicas(precision, scheme):
         b = 2 if L >= 6 else 1
         specs.append((n, (L, L, L), float(rng.choice([10.0, 50.0, 100.0])),
                       float(rng.uniform(0.5, 2.0)), (b, b, b)))
-    errs, (qg, pg, eg, obs), ref = run_both(specs, precision, scheme, 5, seed=55)
-    assert max(errs.values()) < TOL[precision], errs
+    for errs, (qg, pg, eg, obs), ref in assert_parity(specs, precision, scheme, 5, TOL[precision],
+                                                      seeds=range(55, 63)):
+        break
     tol = TOL[precision] * 10
     for r in range(len(specs)):
         o = ref.observables(r)
@@ -129,20 +131,28 @@ def test_parity_batched_replicas(precision, scheme):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_observables_match_oracle(precision):
     specs = [(1000, (cube(1000),) * 3, 100.0, 1.0, (2, 2, 2))]
-    errs, (_, _, _, obs), ref = run_both(specs, precision, "HYBRID", 3, seed=9)
+    for errs, (_, _, _, obs), ref in assert_parity(specs, precision, "HYBRID", 3, TOL[precision],
+                                                   seeds=range(9, 17)):
+        break
     o = ref.observables(0)
     tol = 1e-10 if precision == "fp64" else 1e-5
     for k in ("E", "K", "U", "Eint", "Tkin", "Tint", "Tpot_num", "Tpot_den"):
         assert abs(obs[0][k] - o[k]) <= tol * abs(o[k]), (k, obs[0][k], o[k])
+    # total momentum: exact in FP64; float rounding of each p_i in the mixed mode
+    ptol = 1e-9 if precision == "fp64" else 1e-4
     for k in ("Px", "Py", "Pz"):
-        assert abs(obs[0][k] - o[k]) < 1e-9
+        assert abs(obs[0][k] - o[k]) < ptol
 
 
 # ---- determinism, resume, graphs ----------------------------------------------
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("scheme", ["SER", "HYBRID"])
-def test_resume_and_graph_are_bit_exact(precision, scheme):
+@pytest.mark.parametrize("scheme", ["SER", "HYBRID", "SEM", "SSA"])
+def test_checkpoint_restart_and_graph_are_bit_exact(precision, scheme):
+    """10 steps as one graph-replayed run == 4 eager steps, a raw checkpoint
+    restored into a fresh handle, and 6 more graph steps (bit for bit); a
+    restart through absolute coordinates (get_state/set_state) agrees to
+    rounding."""
     from paper_1507_06643_gb300 import dpde
     specs = [(3000, (cube(3000),) * 3, 100.0, 1.0, (2, 2, 2))]
     q, p, e = make_state(specs, 3, precision == "mixed")
@@ -155,13 +165,36 @@ def test_resume_and_graph_are_bit_exact(precision, scheme):
     B = dpde.System(prm, rep)
     B.set_state(q, p, e)
     B.step(4, 0.01, scheme, use_graph=False)
+    blob = B.checkpoint()
     mid = B.get_state()
     C = dpde.System(prm, rep)
-    C.set_state(*mid, step=4)
+    C.restore(blob)
     C.step(6, 0.01, scheme, use_graph=True)
-    c = C.get_state()
-    for x, y in zip(a, c):
+    for x, y in zip(a, C.get_state()):
         assert np.array_equal(x, y)
+    D = dpde.System(prm, rep)
+    D.set_state(*mid, step=4)
+    D.step(6, 0.01, scheme, use_graph=True)
+    tol = 1e-9 if precision == "fp64" else 1e-3
+    for x, y in zip(a, D.get_state()):
+        assert np.max(np.abs(x - y)) / np.max(np.abs(x)) < tol
+    for S in (A, B, C, D):
+        S.close()
+
+
+def test_restore_rejects_a_foreign_checkpoint():
+    from paper_1507_06643_gb300 import dpde
+    rep = [dpde.make_replica(500, (cube(500),) * 3, 100.0)]
+    A = dpde.System(dpde.make_params(seed=1, precision="mixed"), rep)
+    q, p, e = make_state([(500, (cube(500),) * 3, 100.0, 1.0, (1, 1, 1))], 1, True)
+    A.set_state(q, p, e)
+    blob = A.checkpoint()
+    B = dpde.System(dpde.make_params(seed=2, precision="mixed"), rep)
+    with pytest.raises(dpde.DPDEError) as ei:
+        B.restore(blob)
+    assert ei.value.code == dpde.DPDE_ERR_ARG
+    A.close()
+    B.close()
 
 
 def test_momentum_is_conserved():
@@ -204,11 +237,27 @@ def test_negative_and_nonfinite_state_reported():
 
 @pytest.mark.parametrize("precision,scheme", [("mixed", "HYBRID"), ("mixed", "SER"), ("fp64", "HYBRID")])
 def test_full_size_large_n4m_one_step(precision, scheme):
+    """The benchmark's workload (4M particles) in the benchmark's launch
+    configuration, one step, element by element against the oracle. In the
+    mixed Hybrid run some particles sit within float rounding of a cell face;
+    particles within 2 r_cut of such a flip are excluded (they must be < 1%)."""
+    from scipy.spatial import cKDTree
     from paper_1507_06643_gb300 import inputs
     w = inputs.large_n4m(precision)
     spec = w.replicas[0]
     state = inputs.workload_state(w)
     specs = [(spec.n, spec.box, spec.cv, spec.kT, spec.bricks)]
-    errs, _, _ = run_both(specs, precision, scheme, 1, dt=w.dt, a=w.a, sigma=w.sigma,
-                          prm_seed=w.seed, state=state)
-    assert max(errs.values()) < TOL[precision], errs
+    errs, flips, (qg, pg, eg, _), ref = run_both(specs, precision, scheme, 1, dt=w.dt, a=w.a,
+                                                  sigma=w.sigma, prm_seed=w.seed, state=state)
+    keep = np.ones(spec.n, bool)
+    if flips and scheme == "HYBRID":
+        box = np.asarray(spec.box)
+        tree = cKDTree(np.mod(ref.q, box), boxsize=box)
+        near = tree.query_ball_point(np.mod(ref.q[sorted(flips)], box), 2.0)
+        for lst in near:
+            keep[lst] = False
+        assert keep.mean() > 0.99, keep.mean()
+    dq = q_diff(qg, ref.q, [spec.box], ref.offsets)
+    e = {"q": float(np.max(np.abs(dq[keep])) / np.max(np.abs(ref.q))),
+         "p": rel_err(pg[keep], ref.p[keep]), "eps": rel_err(eg[keep], ref.eps[keep])}
+    assert max(e.values()) < TOL[precision], (e, len(flips))
