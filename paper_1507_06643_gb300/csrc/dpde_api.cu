@@ -28,8 +28,6 @@ struct GraphKey {
     }
 };
 
-constexpr int SSA_RCAP = 1024;   // pairs of one SSA round buffered per brick
-
 }  // namespace
 
 struct dpde_handle {
@@ -41,19 +39,28 @@ struct dpde_handle {
     int ncells = 0;
     int nbricks = 0;
     int nchunks = 0;
-    int kc_max = 1;
-    int ssa_cap = 0;          // particles per brick staged in shared memory
-    size_t ssa_smem = 0;
     int nbr_cap = 0;
     bool mixed = false;
     int need_col3_whole[14] = {0};
+    int need_col3_brick[14] = {0};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t cap_stream = nullptr;
     // device buffers
     void *qA = nullptr, *pA = nullptr, *qB = nullptr, *pB = nullptr, *F = nullptr, *dp = nullptr;
-    void *eA = nullptr, *eB = nullptr, *nbr_w = nullptr;
-    int *cA = nullptr, *cB = nullptr, *nbr_j = nullptr, *nbr_n = nullptr;
+    void *eA = nullptr, *eB = nullptr, *nbr_w = nullptr, *fwd_g = nullptr, *fwd_w = nullptr;
+    int *cA = nullptr, *cB = nullptr, *nbr_j = nullptr, *nbr_n = nullptr, *fwd_j = nullptr, *fwd_n = nullptr;
+    int* fwd_cur = nullptr;
+    int4 *tile_org = nullptr, *tile_dim = nullptr;
+    int ntiles = 0;
+    int kc_max = 1;
+    int ssa_cap = 0;          // particles staged in shared memory per SSA block
+    int ssa_ccap = 0;         // cells per SSA block
+    int nssa_blocks = 0;
+    int4* ssa_blocks = nullptr;   // (replica, first brick, bricks, -)
+    size_t ssa_smem = 0;
+    int hcap = 0;             // halo particles staged per force tile
+    size_t tile_smem = 0;
     uint32_t* idB = nullptr;
     int *key = nullptr, *tmp = nullptr, *cnt = nullptr, *start = nullptr, *bsum = nullptr;
     int *rep_of_slot = nullptr, *rep_of_cell = nullptr, *brick_rep = nullptr, *tab = nullptr;
@@ -104,6 +111,7 @@ Ctx<T> make_ctx(dpde_handle* h) {
     C.key = h->key; C.tmp = h->tmp;
     C.count = h->cnt; C.fill = h->cnt + h->ncells; C.start = h->start;
     C.nbr_j = h->nbr_j; C.nbr_w = (T*)h->nbr_w; C.nbr_n = h->nbr_n; C.nbr_cap = h->nbr_cap;
+    C.fwd_j = h->fwd_j; C.fwd_g = (vec_t<T>*)h->fwd_g; C.fwd_w = (T*)h->fwd_w; C.fwd_n = h->fwd_n; C.fwd_cur = h->fwd_cur;
     C.rep_of_slot = h->rep_of_slot; C.rep_of_cell = h->rep_of_cell;
     C.brick_rep = h->brick_rep; C.tab = h->tab;
     C.reps = h->d_reps; C.step = h->d_step; C.status = h->d_status;
@@ -145,11 +153,23 @@ void enqueue_sort(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T half_dt, T
 }
 
 template <class T>
-void enqueue_ssa_rounds(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_dt) {
-    const int nbc = ceil_div(h->ncells, 128);
+void enqueue_force(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T half_dt, int kick, int list) {
+    const dim3 g(h->ntiles), blk(TILE_THREADS);
+    switch (list) {
+    case LIST_ALL: k_force_tile<T, LIST_ALL><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap); break;
+    case LIST_CROSS: k_force_tile<T, LIST_CROSS><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap); break;
+    case LIST_FWD: k_force_tile<T, LIST_FWD><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap); break;
+    default: k_force_tile<T, LIST_NONE><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap); break;
+    }
+}
+
+template <class T>
+void enqueue_ssa_rounds(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_dt, int whole) {
+    const int nbc = ceil_div(h->ncells, 256);
     for (int di = 0; di < 14; ++di) {
-        const int ncol = di == 0 ? 1 : (h->need_col3_whole[di] ? 3 : 2);
-        for (int col = 0; col < ncol; ++col) k_ssa_round<T><<<nbc, 128, 0, st>>>(C, di, col, dt, sqrt_dt);
+        const int three = whole ? h->need_col3_whole[di] : h->need_col3_brick[di];
+        const int ncol = di == 0 ? 1 : (three ? 3 : 2);
+        for (int col = 0; col < ncol; ++col) k_ssa_round<T><<<nbc, 256, 0, st>>>(C, di, col, whole, dt, sqrt_dt);
     }
 }
 
@@ -159,17 +179,19 @@ void enqueue_step(dpde_handle* h, cudaStream_t st, double dt_d, int scheme) {
     const T dt = (T)dt_d, half_dt = (T)(0.5 * dt_d), sqrt_dt = (T)std::sqrt(dt_d);
     const int nb = ceil_div(h->N, h->block);
     enqueue_sort<T>(h, C, st, half_dt, dt, 1);
-    const int list = scheme == DPDE_SSA ? LIST_NONE : (scheme == DPDE_HYBRID ? LIST_CROSS : LIST_ALL);
+    const int list = scheme == DPDE_SSA ? LIST_FWD : (scheme == DPDE_HYBRID ? LIST_CROSS : LIST_ALL);
     phase(h, st, DPDE_PHASE_FORCE, 0);
-    k_force<T><<<nb, h->block, 0, st>>>(C, half_dt, 1, list);
+    enqueue_force<T>(h, C, st, half_dt, 1, list);
     phase(h, st, DPDE_PHASE_FORCE, 1);
-    if (scheme == DPDE_HYBRID) {
+    if (scheme == DPDE_HYBRID || scheme == DPDE_SSA) {
         phase(h, st, DPDE_PHASE_SSA, 0);
-        k_ssa_brick<T><<<h->nbricks, SSA_THREADS, h->ssa_smem, st>>>(C, dt, sqrt_dt, h->ssa_cap, SSA_RCAP);
-        phase(h, st, DPDE_PHASE_SSA, 1);
-    } else if (scheme == DPDE_SSA) {
-        phase(h, st, DPDE_PHASE_SSA, 0);
-        enqueue_ssa_rounds<T>(h, C, st, dt, sqrt_dt);
+        if (scheme == DPDE_SSA) {
+            k_fwd_gauss<T><<<nb, h->block, 0, st>>>(C);
+            enqueue_ssa_rounds<T>(h, C, st, dt, sqrt_dt, 1);
+        } else {
+            k_ssa_block<T><<<h->nssa_blocks, SSA_THREADS, h->ssa_smem, st>>>(C, h->ssa_blocks, dt, sqrt_dt,
+                                                                              h->ssa_cap, h->ssa_ccap);
+        }
         phase(h, st, DPDE_PHASE_SSA, 1);
     }
     if (scheme == DPDE_SER || scheme == DPDE_HYBRID) {
@@ -182,9 +204,7 @@ void enqueue_step(dpde_handle* h, cudaStream_t st, double dt_d, int scheme) {
     else if (scheme == DPDE_SEM) k_sem<T><<<nb, h->block, 0, st>>>(C, dt, sqrt_dt);
     else k_copy_back<T><<<nb, h->block, 0, st>>>(C);
     phase(h, st, DPDE_PHASE_SWEEP2, 1);
-    phase(h, st, DPDE_PHASE_OTHER, 0);
     k_step_inc<<<1, 1, 0, st>>>(h->d_step);
-    phase(h, st, DPDE_PHASE_OTHER, 1);
 }
 
 void enqueue_step_any(dpde_handle* h, cudaStream_t st, double dt, int scheme) {
@@ -198,7 +218,7 @@ void enqueue_set_state(dpde_handle* h, cudaStream_t st, const double* q, const d
     const int nb = ceil_div(h->N, h->block);
     k_load_state<T><<<nb, h->block, 0, st>>>(C, q, p, e);
     enqueue_sort<T>(h, C, st, T(0), T(0), 0);
-    k_force<T><<<nb, h->block, 0, st>>>(C, T(0), 0, LIST_NONE);
+    enqueue_force<T>(h, C, st, T(0), 0, LIST_NONE);
     k_copy_back<T><<<nb, h->block, 0, st>>>(C);
 }
 
@@ -235,7 +255,7 @@ void free_all(dpde_handle* h) {
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
     void* bufs[] = {h->qA, h->pA, h->qB, h->pB, h->F, h->dp, h->eA, h->eB, h->nbr_w, h->cA, h->cB, h->nbr_j,
-                    h->nbr_n, h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
+                    h->nbr_n, h->fwd_j, h->fwd_g, h->fwd_w, h->fwd_n, h->fwd_cur, h->tile_org, h->tile_dim, h->ssa_blocks, h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
                     h->rep_of_cell, h->brick_rep, h->tab, h->chunk_rep, h->chunk_begin, h->chunk_end,
                     h->rep_chunk_begin, h->partial, h->obs_out, h->d_reps, h->d_step, h->d_status,
                     h->staging, h->cells_out};
@@ -267,7 +287,8 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     long long N = 0, ncells = 0, nbricks = 0;
     const int CHUNK = 4096;
     std::vector<int> chunk_rep, chunk_begin, chunk_end, rep_chunk_begin(1, 0), tabs, brick_rep;
-    double rho_max = 0.0, per_brick_max = 0.0;
+    std::vector<int4> torg, tdim;
+    double rho_max = 0.0, per_cell_max = 0.0, per_brick_max = 0.0;
     for (int r = 0; r < n_replicas; ++r) {
         const dpde_replica& d = replicas[r];
         RepInfo I{};
@@ -313,8 +334,16 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
             for (int c = 0; c < I.nc[a]; ++c) tabs.push_back(c / I.k[a]);
         for (int b = 0; b < nbr; ++b) brick_rep.push_back(r);
         h->kc_max = std::max(h->kc_max, kc);
-        rho_max = std::max(rho_max, (double)d.n / (d.box[0] * d.box[1] * d.box[2]));
         per_brick_max = std::max(per_brick_max, (double)d.n / nbr);
+        for (int z0 = 0; z0 < I.nc[2]; z0 += TILE_EDGE)
+            for (int y0 = 0; y0 < I.nc[1]; y0 += TILE_EDGE)
+                for (int x0 = 0; x0 < I.nc[0]; x0 += TILE_EDGE) {
+                    torg.push_back(make_int4(r, x0, y0, z0));
+                    tdim.push_back(make_int4(std::min(TILE_EDGE, I.nc[0] - x0), std::min(TILE_EDGE, I.nc[1] - y0),
+                                             std::min(TILE_EDGE, I.nc[2] - z0), 0));
+                }
+        per_cell_max = std::max(per_cell_max, (double)d.n / (double)(I.nc[0] * I.nc[1] * I.nc[2]));
+        rho_max = std::max(rho_max, (double)d.n / (d.box[0] * d.box[1] * d.box[2]));
         h->info.push_back(I);
         N += d.n;
         ncells += I.ncells;
@@ -334,21 +363,51 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     h->ncells = (int)ncells;
     h->nbricks = (int)nbricks;
     h->nchunks = (int)chunk_rep.size();
+    h->ntiles = (int)torg.size();
     // neighbour-list capacity: 3x the mean neighbour count of the densest replica, + 32
     const double mean_nbr = 4.0 / 3.0 * M_PI * rho_max * P.r_cut * P.r_cut * P.r_cut;
     h->nbr_cap = (int)std::ceil(3.0 * mean_nbr) + 32;
-    // SSA bricks are staged in shared memory up to 1.3x the mean occupancy + 64
-    // (fuller bricks run in place on global memory)
     const size_t vsz = h->mixed ? sizeof(float4) : sizeof(d4);
     const size_t esz = h->mixed ? sizeof(ff) : sizeof(double);
-    const size_t tsz0 = h->mixed ? sizeof(float) : sizeof(double);
-    const size_t per = 2 * vsz + esz;
-    const size_t head = ((size_t)(3 * h->kc_max + 2) * sizeof(int) + 31) & ~(size_t)31;
-    const size_t rbuf = (size_t)SSA_RCAP * (2 * sizeof(int) + 4 * tsz0) + 16;
-    const size_t smem_limit = 200 * 1024;
-    h->ssa_cap = (int)std::max<double>(
-        0.0, std::min<double>(1.3 * per_brick_max + 64.0, (double)((smem_limit - head - rbuf) / per)));
-    h->ssa_smem = 32 + head + (size_t)h->ssa_cap * per + rbuf;   // + 32: base alignment slack
+    // SSA blocks: runs of consecutive bricks of one replica whose particles
+    // (1.1x the mean occupancy) fill the shared-memory budget
+    std::vector<int4> sblk;
+    {
+        const size_t tsz1 = h->mixed ? sizeof(float) : sizeof(double);
+        const size_t per = 3 * tsz1 + esz + 1;
+        const size_t budget = 200 * 1024;
+        int nbmax = 1;
+        for (int r = 0; r < h->R; ++r) {
+            const RepInfo& I = h->info[r];
+            const int kc = I.k[0] * I.k[1] * I.k[2];
+            const int nbr = I.B[0] * I.B[1] * I.B[2];
+            const double per_brick = 1.1 * (double)I.n / nbr + 16.0;
+            const double bytes_brick = per_brick * per + kc * sizeof(int);
+            int nb = (int)std::max(1.0, std::floor((double)(budget - 64) / bytes_brick));
+            nb = std::min(nb, nbr);
+            nbmax = std::max(nbmax, nb);
+            for (int b0 = 0; b0 < nbr; b0 += nb) sblk.push_back(make_int4(r, I.brick_off + b0, std::min(nb, nbr - b0), 0));
+        }
+        h->nssa_blocks = (int)sblk.size();
+        h->ssa_ccap = nbmax * h->kc_max;
+        const size_t head = ((size_t)(h->ssa_ccap + 1) * sizeof(int) + 15) & ~(size_t)15;
+        h->ssa_cap = (int)std::max<double>(0.0, std::min<double>(255.0 * 1024 * 1024,
+                                                                 (double)((budget - head - 16) / per)));
+        h->ssa_smem = 16 + head + (size_t)h->ssa_cap * per + 16;
+    }
+    // force tiles: halo of (TILE_EDGE + 2)^3 cells staged up to 1.15x the mean + 64
+    {
+        const size_t vsz0 = vsz;
+        const int hcmax = (TILE_EDGE + 2) * (TILE_EDGE + 2) * (TILE_EDGE + 2);
+        const size_t thead =
+            (((size_t)(3 * hcmax + 1 + 66 + HIT_BUF * TILE_THREADS) * sizeof(int)) + 31) & ~(size_t)31;
+        const size_t tper = vsz0 + 2 * sizeof(unsigned short);
+        const double mean_halo = per_cell_max * hcmax;
+        const size_t smem_limit = 200 * 1024;
+        h->hcap = (int)std::min<double>(std::min<double>(1.15 * mean_halo + 64.0, 65535.0),
+                                        (double)((smem_limit - thead) / tper));
+        h->tile_smem = 32 + thead + (size_t)h->hcap * tper;
+    }
     // colours per SSA direction for the whole-replica SSA: three when the
     // leading axis has an odd number of cells
     static const int dirs[14][3] = {{0, 0, 0},   {1, 0, 0},  {-1, 1, 0}, {0, 1, 0},  {1, 1, 0},
@@ -356,8 +415,10 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
                                     {1, 0, 1},   {-1, 1, 1}, {0, 1, 1},  {1, 1, 1}};
     for (int di = 1; di < 14; ++di) {
         const int lead = dirs[di][2] ? 2 : (dirs[di][1] ? 1 : 0);
-        for (const RepInfo& I : h->info)
+        for (const RepInfo& I : h->info) {
             if (I.nc[lead] & 1) h->need_col3_whole[di] = 1;
+            if (I.B[lead] == 1 && (I.k[lead] & 1)) h->need_col3_brick[di] = 1;
+        }
     }
     auto bail = [&](cudaError_t e, const char* what) {
         std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
@@ -394,6 +455,13 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     CKC(cudaMalloc(&h->nbr_j, sizeof(int) * n1 * (size_t)h->nbr_cap));
     CKC(cudaMalloc(&h->nbr_w, tsz * n1 * (size_t)h->nbr_cap));
     CKC(cudaMalloc(&h->nbr_n, sizeof(int) * n1));
+    CKC(cudaMalloc(&h->fwd_j, sizeof(int) * n1 * (size_t)h->nbr_cap));
+    CKC(cudaMalloc(&h->fwd_g, vsz * n1 * (size_t)h->nbr_cap));
+    CKC(cudaMalloc(&h->fwd_w, tsz * n1 * (size_t)h->nbr_cap));
+    CKC(cudaMalloc(&h->fwd_n, sizeof(int) * n1));
+    CKC(cudaMalloc(&h->fwd_cur, sizeof(int) * n1));
+    CKC(cudaMalloc(&h->tile_org, sizeof(int4) * torg.size()));
+    CKC(cudaMalloc(&h->tile_dim, sizeof(int4) * tdim.size()));
     CKC(cudaMalloc(&h->key, sizeof(int) * n1));
     CKC(cudaMalloc(&h->tmp, sizeof(int) * n1));
     CKC(cudaMalloc(&h->cnt, sizeof(int) * 2 * c1));
@@ -425,6 +493,8 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         CKC(cudaMemcpy(h->rep_of_cell, roc.data(), sizeof(int) * c1, cudaMemcpyHostToDevice));
         CKC(cudaMemcpy(h->brick_rep, brick_rep.data(), sizeof(int) * brick_rep.size(), cudaMemcpyHostToDevice));
         CKC(cudaMemcpy(h->tab, tabs.data(), sizeof(int) * tabs.size(), cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(h->tile_org, torg.data(), sizeof(int4) * torg.size(), cudaMemcpyHostToDevice));
+        CKC(cudaMemcpy(h->tile_dim, tdim.data(), sizeof(int4) * tdim.size(), cudaMemcpyHostToDevice));
         if (!chunk_rep.empty()) {
             CKC(cudaMemcpy(h->chunk_rep, chunk_rep.data(), sizeof(int) * chunk_rep.size(), cudaMemcpyHostToDevice));
             CKC(cudaMemcpy(h->chunk_begin, chunk_begin.data(), sizeof(int) * chunk_rep.size(), cudaMemcpyHostToDevice));
@@ -441,11 +511,29 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         CKC(cudaMemset(h->cA, 0, sizeof(int) * n1));
         CKC(cudaMemset(h->F, 0, vsz * n1));
         CKC(cudaMemset(h->nbr_n, 0, sizeof(int) * n1));
+        CKC(cudaMemset(h->fwd_n, 0, sizeof(int) * n1));
+        CKC(cudaMemset(h->fwd_cur, 0, sizeof(int) * n1));
     }
+    CKC(cudaMalloc(&h->ssa_blocks, sizeof(int4) * sblk.size()));
+    CKC(cudaMemcpy(h->ssa_blocks, sblk.data(), sizeof(int4) * sblk.size(), cudaMemcpyHostToDevice));
     if (h->mixed)
-        CKC(cudaFuncSetAttribute(k_ssa_brick<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ssa_smem));
+        CKC(cudaFuncSetAttribute(k_ssa_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ssa_smem));
     else
-        CKC(cudaFuncSetAttribute(k_ssa_brick<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ssa_smem));
+        CKC(cudaFuncSetAttribute(k_ssa_block<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ssa_smem));
+    {
+        const int sm = (int)h->tile_smem;
+        if (h->mixed) {
+            CKC(cudaFuncSetAttribute(k_force_tile<float, LIST_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            CKC(cudaFuncSetAttribute(k_force_tile<float, LIST_ALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            CKC(cudaFuncSetAttribute(k_force_tile<float, LIST_CROSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            CKC(cudaFuncSetAttribute(k_force_tile<float, LIST_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        } else {
+            CKC(cudaFuncSetAttribute(k_force_tile<double, LIST_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            CKC(cudaFuncSetAttribute(k_force_tile<double, LIST_ALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            CKC(cudaFuncSetAttribute(k_force_tile<double, LIST_CROSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            CKC(cudaFuncSetAttribute(k_force_tile<double, LIST_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        }
+    }
 #undef CKC
     *out = h;
     return DPDE_OK;

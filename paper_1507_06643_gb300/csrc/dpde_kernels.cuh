@@ -11,7 +11,7 @@
 
 namespace dpde {
 
-enum ListMode : int { LIST_NONE = 0, LIST_ALL = 1, LIST_CROSS = 2 };
+enum ListMode : int { LIST_NONE = 0, LIST_ALL = 1, LIST_CROSS = 2, LIST_FWD = 3 };
 
 template <class T> struct Ctx {
     using vec = vec_t<T>;
@@ -29,6 +29,12 @@ template <class T> struct Ctx {
     T* nbr_w;        // 1 - r/r_cut of each entry
     int* nbr_n;      // entries per particle
     int nbr_cap;
+    int* fwd_j;      // forward pairs of the SSA, [k * N + i],
+                     //   packed t | direction << 27, in (direction, t) order
+    T* fwd_w;        //   w = 1 - r/r_cut of each entry
+    vec* fwd_g;      //   G_it of each entry (x, y, z)
+    int* fwd_n;
+    int* fwd_cur;    // SSA cursor into each forward list
     const int* rep_of_slot;
     const int* rep_of_cell;
     const int* brick_rep;
@@ -361,24 +367,88 @@ __global__ void k_copy_back(Ctx<T> C) {
 
 // ---------------------------------------------------------------------------
 // conservative forces F(q) on B (soft repulsion a (1 - r/r_cut) r_hat), the
-// second Verlet half-kick p += dt/2 F when kick != 0, and the neighbour list
-// of the FD part (all pairs, or only cross-brick pairs for Hybrid's SER).
-//
-// Pass 1 walks the 27 neighbour cells as one flattened loop over 27 slot
-// segments (so the lanes of a warp stay converged whatever the per-cell
-// counts) and appends every particle within r_cut to the list, packed with
-// its segment code. Pass 2 runs over these hits only (uniform trip counts):
-// force, w = 1 - r/r_cut, and the final list (compacted to cross-brick
-// entries for Hybrid). The two passes visit neighbours in the same order, so
-// the force sums are deterministic.
+// second Verlet half-kick p += dt/2 F when kick != 0, and the lists of the
+// fluctuation/dissipation part:
+//   LIST_ALL   every neighbour (j, w = 1 - r/r_cut)           -> nbr
+//   LIST_CROSS neighbours in another brick                      -> nbr
+//              and forward neighbours in the same brick         -> fwd
+//   LIST_FWD   forward neighbours (whole-replica SSA)           -> fwd
+// A forward neighbour of i lies in the half stencil (segment > 13) or in
+// i's own cell after i; its segment - 13 is the SSA direction index, and the
+// visiting order (segment, slot) is the SSA sequence order of i's pairs.
+// Segment s = 9 (dz+1) + 3 (dy+1) + (dx+1) for the neighbour cell offset.
 // ---------------------------------------------------------------------------
-constexpr int NBR_J_BITS = 27;   // slot index bits of a packed pass-1 entry
+constexpr int NBR_J_BITS = 27;   // slot bits of a packed forward entry
 constexpr int NBR_J_MASK = (1 << NBR_J_BITS) - 1;
 
+template <class T> __device__ __forceinline__ T trsqrt(T x);
+template <> __device__ __forceinline__ float trsqrt(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double trsqrt(double x) { return rsqrt(x); }
+
 template <class T>
-__global__ void __launch_bounds__(256) k_force(Ctx<T> C, T half_dt, int kick, int list_mode) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= C.N) return;
+struct PairOut {
+    T fx = 0, fy = 0, fz = 0;
+    int nn = 0, nf = 0;
+};
+
+// one neighbour j (global slot) of i at separation d with |d|^2 = r2
+struct NoiseKey {
+    uint32_t step, rep, id_i;
+};
+
+template <class T, int LM>
+__device__ __forceinline__ void force_hit(const Ctx<T>& C, int i, int j, uint32_t id_j, const NoiseKey& nk,
+                                          int seg, bool cross, T dx, T dy, T dz, T r2, PairOut<T>& o) {
+    const size_t N = (size_t)C.N;
+    T w = T(1);
+    if (r2 > T(0)) {
+        const T ir = trsqrt(r2);
+        w = T(1) - r2 * ir * C.inv_rc;
+        const T f = C.a * w * ir;
+        o.fx += f * dx; o.fy += f * dy; o.fz += f * dz;
+    }
+    if (LM == LIST_ALL || (LM == LIST_CROSS && cross)) {
+        if (o.nn < C.nbr_cap) {
+            C.nbr_j[(size_t)o.nn * N + i] = j;
+            C.nbr_w[(size_t)o.nn * N + i] = w;
+        }
+        ++o.nn;
+    } else if ((LM == LIST_CROSS || LM == LIST_FWD) && (seg > 13 || (seg == 13 && j > i))) {
+        if (o.nf < C.nbr_cap) {
+            const size_t at = (size_t)o.nf * N + i;
+            C.fwd_j[at] = j | ((seg - 13) << NBR_J_BITS);
+            C.fwd_w[at] = w;
+        }
+        ++o.nf;
+    }
+}
+
+template <class T, int LM>
+__device__ __forceinline__ void force_finish(const Ctx<T>& C, int i, T half_dt, int kick, PairOut<T>& o) {
+    if (o.nn > C.nbr_cap || o.nf > C.nbr_cap) {
+        flag(C.status, ST_CAPACITY);
+        o.nn = min(o.nn, C.nbr_cap);
+        o.nf = min(o.nf, C.nbr_cap);
+    }
+    if (LM == LIST_ALL || LM == LIST_CROSS) C.nbr_n[i] = o.nn;
+    if (LM == LIST_CROSS || LM == LIST_FWD) {
+        C.fwd_n[i] = o.nf;
+        C.fwd_cur[i] = 0;
+    }
+    vec_t<T> f;
+    f.x = o.fx; f.y = o.fy; f.z = o.fz; f.w = T(0);
+    C.F[i] = f;
+    if (kick) {
+        vec_t<T> pv = C.pB[i];
+        pv.x += half_dt * o.fx; pv.y += half_dt * o.fy; pv.z += half_dt * o.fz;
+        C.pB[i] = pv;
+    }
+}
+
+// Per-particle path on global memory (fallback for tiles whose halo does
+// not fit in shared memory).
+template <class T, int LM>
+__device__ void force_one_global(const Ctx<T>& C, int i, T half_dt, int kick) {
     const RepInfo& R = C.reps[C.rep_of_slot[i]];
     const vec_t<T> qi = C.qB[i];
     const int cc = C.cB[i];
@@ -387,98 +457,192 @@ __global__ void __launch_bounds__(256) k_force(Ctx<T> C, T half_dt, int kick, in
     const T lx = cell_len<T>(R, 0), ly = cell_len<T>(R, 1), lz = cell_len<T>(R, 2);
     const int* bt = brick_tab(C.tab, R);
     const int bx = __ldg(bt + cx), by = __ldg(bt + nx + cy), bz = __ldg(bt + nx + ny + cz);
-    const int xm = cx == 0 ? nx - 1 : cx - 1;
-    const int xp = cx == nx - 1 ? 0 : cx + 1;
-    const bool xcm = __ldg(bt + xm) != bx, xcp = __ldg(bt + xp) != bx;
-    // segment table: segment s = 9 (dz+1) + 3 (dy+1) + (dx+1)
-    int sb[27], se[27];
-    unsigned cross = 0;
-#pragma unroll
-    for (int r = 0; r < 9; ++r) {
-        const int dz = r / 3 - 1, dy = r % 3 - 1;
-        int z = cz + dz;
-        z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
-        int y = cy + dy;
+    const NoiseKey nk{(uint32_t)*C.step, (uint32_t)C.rep_of_slot[i], id_of(qi)};
+    PairOut<T> o;
+    for (int sg = 0; sg < 27; ++sg) {
+        const int dxc = sg % 3 - 1, dyc = (sg / 3) % 3 - 1, dzc = sg / 9 - 1;
+        int x = cx + dxc, y = cy + dyc, z = cz + dzc;
+        x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
         y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-        const bool rc = (__ldg(bt + nx + ny + z) != bz) || (__ldg(bt + nx + y) != by);
-        const int c0 = cell_index(C.tab, R, xm, y, z);
-        const int c1 = cell_index(C.tab, R, cx, y, z);
-        const int c2 = cell_index(C.tab, R, xp, y, z);
-        sb[3 * r] = C.start[c0];
-        se[3 * r] = C.start[c0 + 1];
-        sb[3 * r + 1] = C.start[c1];
-        se[3 * r + 1] = C.start[c1 + 1];
-        sb[3 * r + 2] = C.start[c2];
-        se[3 * r + 2] = C.start[c2 + 1];
-        cross |= (unsigned)(rc || xcm) << (3 * r);
-        cross |= (unsigned)rc << (3 * r + 1);
-        cross |= (unsigned)(rc || xcp) << (3 * r + 2);
-    }
-    // pass 1: candidates within r_cut -> packed (slot, segment) entries
-    const size_t N = (size_t)C.N;
-    int nh = 0;
-    int seg = 0, j = sb[0], je = se[0];
-    T sx = -lx, sy = -ly, sz = -lz;
-    while (true) {
-        while (j >= je) {
-            if (++seg == 27) break;
-            j = sb[seg];
-            je = se[seg];
-            const int dxs = seg % 3 - 1, dys = (seg / 3) % 3 - 1, dzs = seg / 9 - 1;
-            sx = shift<T>(dxs, lx);
-            sy = shift<T>(dys, ly);
-            sz = shift<T>(dzs, lz);
-        }
-        if (seg == 27) break;
-        if (j != i) {
+        z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+        const bool cross = __ldg(bt + x) != bx || __ldg(bt + nx + y) != by || __ldg(bt + nx + ny + z) != bz;
+        const int c = cell_index(C.tab, R, x, y, z);
+        const T sx = shift<T>(dxc, lx), sy = shift<T>(dyc, ly), sz = shift<T>(dzc, lz);
+        const int e = C.start[c + 1];
+        for (int j = C.start[c]; j < e; ++j) {
+            if (j == i) continue;
             const vec_t<T> qj = C.qB[j];
-            const T ddx = (qi.x - qj.x) - sx;
-            const T ddy = (qi.y - qj.y) - sy;
-            const T ddz = (qi.z - qj.z) - sz;
+            const T ddx = (qi.x - qj.x) - sx, ddy = (qi.y - qj.y) - sy, ddz = (qi.z - qj.z) - sz;
             const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-            if (r2 < C.rc2) {
-                if (nh < C.nbr_cap) C.nbr_j[(size_t)nh * N + i] = j | (seg << NBR_J_BITS);
-                ++nh;
+            if (r2 < C.rc2) force_hit<T, LM>(C, i, j, id_of(qj), nk, sg, cross, ddx, ddy, ddz, r2, o);
+        }
+    }
+    force_finish<T, LM>(C, i, half_dt, kick, o);
+}
+
+// Tiled force pass: one block per tile of (up to) 6 x 6 x 6 cells. The tile
+// and its one-cell halo are staged in shared memory in x-fastest halo-cell
+// order, so the three x-cells of each (dy, dz) neighbour row of a particle
+// form one contiguous range. The lanes of a warp walk the 9 rows in step;
+// the candidate loop only records hits (halo index and segment) in a
+// per-thread shared buffer, and a second loop over the hits computes forces
+// and lists -- so the costly part runs once per neighbour, not once per
+// candidate of the slowest lane. Halos larger than hcap fall back to the
+// global path.
+constexpr int TILE_THREADS = 256;
+constexpr int TILE_EDGE = 6;
+constexpr int HIT_BUF = 24;
+
+template <class T, int LM>
+__global__ void __launch_bounds__(TILE_THREADS) k_force_tile(Ctx<T> C, const int4* __restrict__ tile_org,
+                                                             const int4* __restrict__ tile_dim, T half_dt,
+                                                             int kick, int hcap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((size_t)smem_raw + 31) & ~(size_t)31);
+    using vec = vec_t<T>;
+    const int4 org = tile_org[blockIdx.x];
+    const int4 dim = tile_dim[blockIdx.x];
+    const RepInfo& R = C.reps[org.x];
+    const int HX = dim.x + 2, HY = dim.y + 2, HZ = dim.z + 2;
+    const int HC = HX * HY * HZ;
+    const int nx = R.nc[0], ny = R.nc[1], nz = R.nc[2];
+    // shared layout (sized for HC <= (TILE_EDGE+2)^3):
+    //   hstart[HC+1] gstart[HC] hbrick[HC] rowoff[65] nown | hits[HIT_BUF][TILE_THREADS] |
+    //   q[hcap] hcell[hcap] own[hcap]
+    constexpr int HCMAX = (TILE_EDGE + 2) * (TILE_EDGE + 2) * (TILE_EDGE + 2);
+    int* hstart = (int*)smem;
+    int* gstart = hstart + HCMAX + 1;
+    int* hbrick = gstart + HCMAX;
+    int* rowoff = hbrick + HCMAX;
+    int* nown = rowoff + 65;
+    unsigned* hits = (unsigned*)(nown + 1);
+    const size_t head = (((size_t)(3 * HCMAX + 1 + 66 + HIT_BUF * TILE_THREADS) * sizeof(int)) + 31) & ~(size_t)31;
+    vec* hq = (vec*)(smem + head);
+    unsigned short* hcell = (unsigned short*)(hq + hcap);
+    unsigned short* own = hcell + hcap;
+    const int* bt = brick_tab(C.tab, R);
+    // 1. halo cells: global start, count, brick
+    for (int h = threadIdx.x; h < HC; h += blockDim.x) {
+        const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+        int x = org.y + hx - 1, y = org.z + hy - 1, z = org.w + hz - 1;
+        x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+        y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+        z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+        const int c = cell_index(C.tab, R, x, y, z);
+        gstart[h] = C.start[c];
+        hstart[h] = C.start[c + 1] - C.start[c];
+        hbrick[h] = __ldg(bt + x) | (__ldg(bt + nx + y) << 10) | (__ldg(bt + nx + ny + z) << 20);
+    }
+    __syncthreads();
+    // 2. exclusive scan of the halo counts (HC <= 512: two values per thread)
+    {
+        __shared__ int sh[32];
+        const int h0 = 2 * threadIdx.x, h1 = h0 + 1;
+        const int v0 = h0 < HC ? hstart[h0] : 0, v1 = h1 < HC ? hstart[h1] : 0;
+        int total;
+        const int ex = block_exclusive_scan(v0 + v1, sh, total);
+        if (h0 < HC) hstart[h0] = ex;
+        if (h1 < HC) hstart[h1] = ex + v0;
+        if (threadIdx.x == 0) hstart[HC] = total;
+    }
+    __syncthreads();
+    const int H = hstart[HC];
+    const bool staged = H <= hcap;
+    // 3. stage the halo particles; 4. own-row offsets
+    if (staged) {
+        for (int h = threadIdx.x; h < HC; h += blockDim.x) {
+            const int b = hstart[h], n = hstart[h + 1] - b, g = gstart[h];
+            for (int k = 0; k < n; ++k) {
+                hq[b + k] = C.qB[g + k];
+                hcell[b + k] = (unsigned short)h;
             }
         }
-        ++j;
     }
-    if (nh > C.nbr_cap) {
-        flag(C.status, ST_CAPACITY);
-        nh = C.nbr_cap;
-    }
-    // pass 2: forces and the FD neighbour list
-    T fx = 0, fy = 0, fz = 0;
-    int nn = 0;
-    for (int k = 0; k < nh; ++k) {
-        const int packed = C.nbr_j[(size_t)k * N + i];
-        const int jj = packed & NBR_J_MASK;
-        const int sg = (int)((unsigned)packed >> NBR_J_BITS);
-        const vec_t<T> qj = C.qB[jj];
-        const T ddx = (qi.x - qj.x) - shift<T>(sg % 3 - 1, lx);
-        const T ddy = (qi.y - qj.y) - shift<T>((sg / 3) % 3 - 1, ly);
-        const T ddz = (qi.z - qj.z) - shift<T>(sg / 9 - 1, lz);
-        const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-        const T r = tsqrt(r2);
-        const T w = T(1) - r * C.inv_rc;
-        if (r2 > T(0)) {
-            const T f = C.a * w / r;
-            fx += f * ddx; fy += f * ddy; fz += f * ddz;
+    const int nrow = dim.y * dim.z;
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int r = 0; r < nrow; ++r) {
+            rowoff[r] = acc;
+            const int h = ((r / dim.y + 1) * HY + (r % dim.y + 1)) * HX;
+            acc += hstart[h + dim.x + 1] - hstart[h + 1];
         }
-        if (list_mode == LIST_ALL || (list_mode == LIST_CROSS && ((cross >> sg) & 1u))) {
-            C.nbr_j[(size_t)nn * N + i] = jj;
-            C.nbr_w[(size_t)nn * N + i] = w;
-            ++nn;
-        }
+        rowoff[nrow] = acc;
+        *nown = acc;
     }
-    if (list_mode != LIST_NONE) C.nbr_n[i] = nn;
-    vec_t<T> f;
-    f.x = fx; f.y = fy; f.z = fz; f.w = T(0);
-    C.F[i] = f;
-    if (kick) {
-        vec_t<T> pv = C.pB[i];
-        pv.x += half_dt * fx; pv.y += half_dt * fy; pv.z += half_dt * fz;
-        C.pB[i] = pv;
+    __syncthreads();
+    if (!staged) {
+        // fallback: own particles through the global path
+        for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
+            const int h = ((r / dim.y + 1) * HY + (r % dim.y + 1)) * HX;
+            for (int hc = h + 1; hc <= h + dim.x; ++hc) {
+                const int g = gstart[hc], n = hstart[hc + 1] - hstart[hc];
+                for (int k = 0; k < n; ++k) force_one_global<T, LM>(C, g + k, half_dt, kick);
+            }
+        }
+        return;
+    }
+    for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
+        const int h = ((r / dim.y + 1) * HY + (r % dim.y + 1)) * HX;
+        const int b = hstart[h + 1], e = hstart[h + dim.x + 1];
+        for (int k = b; k < e; ++k) own[rowoff[r] + (k - b)] = (unsigned short)k;
+    }
+    __syncthreads();
+    // 5. each own particle: rows in step, hits recorded, then processed
+    const T lx = cell_len<T>(R, 0), ly = cell_len<T>(R, 1), lz = cell_len<T>(R, 2);
+    const uint32_t step = (uint32_t)*C.step;
+    const int no = *nown;
+    unsigned* myhits = hits + threadIdx.x;
+    for (int k0 = 0; k0 < no; k0 += blockDim.x) {
+        const int k = k0 + threadIdx.x;
+        const bool act = k < no;
+        const int hi = act ? own[k] : 0;
+        const int hc = hcell[hi];
+        const int i = gstart[hc] + (hi - hstart[hc]);
+        const vec qi = hq[hi];
+        const int hx = hc % HX, hy = (hc / HX) % HY, hz = hc / (HX * HY);
+        const int mybrick = hbrick[hc];
+        const NoiseKey nk{step, (uint32_t)org.x, id_of(qi)};
+        PairOut<T> o;
+        int nh = 0;
+        auto flush = [&]() {
+            for (int u = 0; u < nh; ++u) {
+                const unsigned e = myhits[u * TILE_THREADS];
+                const int hj = (int)(e & 0xffffu);
+                const int seg = (int)(e >> 16);
+                const int dxc = seg % 3 - 1, dyc = (seg / 3) % 3 - 1, dzc = seg / 9 - 1;
+                const vec qj = hq[hj];
+                const T ddx = (qi.x - qj.x) - shift<T>(dxc, lx);
+                const T ddy = (qi.y - qj.y) - shift<T>(dyc, ly);
+                const T ddz = (qi.z - qj.z) - shift<T>(dzc, lz);
+                const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                const int hcj = hcell[hj];
+                const int j = gstart[hcj] + (hj - hstart[hcj]);
+                force_hit<T, LM>(C, i, j, id_of(qj), nk, seg, hbrick[hcj] != mybrick, ddx, ddy, ddz, r2, o);
+            }
+            nh = 0;
+        };
+        for (int row = 0; row < 9; ++row) {
+            const int dyr = row % 3 - 1, dzr = row / 3 - 1;
+            const int base = ((hz + dzr) * HY + (hy + dyr)) * HX + hx - 1;
+            const int b1 = hstart[base + 1], b2 = hstart[base + 2];
+            const int je = act ? hstart[base + 3] : 0;
+            const T sy = shift<T>(dyr, ly), sz = shift<T>(dzr, lz);
+            for (int j = act ? hstart[base] : 0; j < je; ++j) {
+                if (j == hi) continue;
+                const vec qj = hq[j];
+                const int dxc = (j >= b1) + (j >= b2) - 1;
+                const T ddx = (qi.x - qj.x) - shift<T>(dxc, lx);
+                const T ddy = (qi.y - qj.y) - sy;
+                const T ddz = (qi.z - qj.z) - sz;
+                if (ddx * ddx + ddy * ddy + ddz * ddz < C.rc2) {
+                    if (nh == HIT_BUF) flush();
+                    myhits[nh * TILE_THREADS] = (unsigned)j | ((unsigned)(3 * row + dxc + 1) << 16);
+                    ++nh;
+                }
+            }
+        }
+        flush();
+        if (act) force_finish<T, LM>(C, i, half_dt, kick, o);
     }
 }
 
@@ -648,234 +812,239 @@ __device__ __forceinline__ void ssa_apply(const Ctx<T>& C, const RepInfo& R, vec
     e[t] = eps_add(et, -dK);
 }
 
+// One round (direction di, colour col) of the SSA sequence, as one launch
+// over every cell of every replica. The pairs of cell pair (c, c + delta_di)
+// are the direction-di entries of the forward lists of c's particles, in
+// sequence order; a per-particle cursor walks each forward list across the
+// rounds. Cell pairs of a round touch disjoint particles, so the pair maps
+// update set B in place. whole_box: the domain is the whole replica (the
+// DPDE_SSA scheme) rather than the brick (Hybrid's set A).
 template <class T>
-__device__ __forceinline__ void ssa_pair(const Ctx<T>& C, const RepInfo& R, uint32_t rep, uint32_t step,
-                                         vec_t<T>* p, eps_t<T>* e, int s, int t, uint32_t ids,
-                                         uint32_t idt, T r2, T dt, T sqrt_dt) {
-    const T w = T(1) - tsqrt(r2) * C.inv_rc;
-    ssa_apply(C, R, p, e, s, t, w, pair_gauss<T>(C.seed, step, rep, ids, idt), dt, sqrt_dt);
+__global__ void k_ssa_round(Ctx<T> C, int di, int col, int whole_box, T dt, T sqrt_dt) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C.ncells) return;
+    const int b = C.start[c], e = C.start[c + 1];
+    if (b == e) return;
+    const int rep = C.rep_of_cell[c];
+    const RepInfo& R = C.reps[rep];
+    if (di > 0) {
+        // colour: coordinate of c along the leading axis, inside its domain
+        const int kx = R.k[0], ky = R.k[1], kz = R.k[2];
+        const int kc = kx * ky * kz;
+        const int rel = c - R.cell_off;
+        const int bi = rel / kc, li = rel - bi * kc;
+        const int dyo = c_dirs[di][1], dzo = c_dirs[di][2];
+        const int lead = dzo != 0 ? 2 : (dyo != 0 ? 1 : 0);
+        int l, kl, Bl;
+        if (lead == 0) {
+            l = li % kx; kl = kx; Bl = R.B[0];
+            if (whole_box) l += (bi % R.B[0]) * kx;
+        } else if (lead == 1) {
+            l = (li / kx) % ky; kl = ky; Bl = R.B[1];
+            if (whole_box) l += ((bi / R.B[0]) % R.B[1]) * ky;
+        } else {
+            l = li / (kx * ky); kl = kz; Bl = R.B[2];
+            if (whole_box) l += (bi / (R.B[0] * R.B[1])) * kz;
+        }
+        if (whole_box) { kl = R.nc[lead]; Bl = 1; }
+        const bool odd = (Bl == 1) && (kl & 1);
+        const int my = (odd && l == kl - 1) ? 2 : (l & 1);
+        if (my != col) return;
+    }
+    for (int s = b; s < e; ++s) {
+        const int nf = C.fwd_n[s];
+        int m = C.fwd_cur[s];
+        for (; m < nf; ++m) {
+            const size_t at = (size_t)m * C.N + s;
+            const int packed = C.fwd_j[at];
+            if ((packed >> NBR_J_BITS) != di) break;
+            const vec_t<T> g = C.fwd_g[at];
+            ssa_apply(C, R, C.pB, C.eB, s, packed & NBR_J_MASK, C.fwd_w[at], T3<T>{g.x, g.y, g.z}, dt, sqrt_dt);
+        }
+        C.fwd_cur[s] = m;
+    }
 }
 
-constexpr int SSA_THREADS = 256;
-
-// One Hybrid domain ("brick") per block: the brick's particles (a contiguous
-// slot range in brick-major cell order) are staged in shared memory when
-// they fit (else the block works on global memory in place), then the SSA
-// sequence runs round by round (14 directions x 2-3 colours). The cell
-// pairs of a round touch disjoint particles. Each round has three phases:
-//  (a) every cell pair lists its interacting pairs, in sequence order, into
-//      a shared round buffer (w = 1 - r/r_cut);
-//  (b) all lanes draw the Gaussians of the round's pairs;
-//  (c) each cell pair applies its pair maps in order.
-// A cell pair whose pairs do not fit in the buffer redoes its scan in (c)
-// with inline Gaussians. Updates set B in place and refreshes beta.
+// Gaussians of the forward entries of particles [s0, s1) (state
+// independent: drawn ahead of the sequential SSA rounds, all lanes busy).
 template <class T>
-__global__ void __launch_bounds__(SSA_THREADS) k_ssa_brick(Ctx<T> C, T dt, T sqrt_dt, int cap, int rcap) {
+__device__ __forceinline__ void draw_forward_gaussians(const Ctx<T>& C, int s0, int s1, uint32_t rep) {
+    const uint32_t step = (uint32_t)*C.step;
+    const size_t N = (size_t)C.N;
+    for (int s = s0 + (int)threadIdx.x; s < s1; s += blockDim.x) {
+        const int nf = C.fwd_n[s];
+        const uint32_t ids = C.idB[s];
+        for (int m = 0; m < nf; ++m) {
+            const size_t at = (size_t)m * N + s;
+            const int t = C.fwd_j[at] & NBR_J_MASK;
+            const T3<T> G = pair_gauss<T>(C.seed, step, rep, ids, C.idB[t]);
+            vec_t<T> g;
+            g.x = G.x; g.y = G.y; g.z = G.z; g.w = T(0);
+            C.fwd_g[at] = g;
+        }
+    }
+}
+
+// Hybrid's SSA over set A. A block owns a run of consecutive domains
+// ("bricks") of one replica -- a contiguous slot range in brick-major cell
+// order -- so that every round has thousands of independent cell pairs
+// between two barriers. Momenta (as x, y, z arrays) and internal energies
+// are staged in shared memory when they fit (else the block works on
+// global memory in place). After the Gaussians are drawn, the rounds
+// (direction di, colour col) run: each thread takes cell pairs
+// (c, c + delta_di) of colour col and applies, in sequence order, the
+// direction-di forward entries of c's particles. Writes set B back with
+// beta refreshed.
+constexpr int SSA_THREADS = 1024;
+
+template <class T>
+__global__ void __launch_bounds__(SSA_THREADS) k_ssa_block(Ctx<T> C, const int4* __restrict__ blocks, T dt,
+                                                           T sqrt_dt, int pcap, int ccap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using vec = vec_t<T>;
     using E = eps_t<T>;
-    // 32-byte aligned base (d4 vectors); the launch adds 32 bytes of slack
-    unsigned char* smem = (unsigned char*)(((size_t)smem_raw + 31) & ~(size_t)31);
-    const int g = blockIdx.x;
-    const int rep = C.brick_rep[g];
+    const int4 blk = blocks[blockIdx.x];   // (replica, first brick, number of bricks, -)
+    const int rep = blk.x;
     const RepInfo& R = C.reps[rep];
     const int kx = R.k[0], ky = R.k[1], kz = R.k[2];
     const int kc = kx * ky * kz;
-    const int first = R.cell_off + (g - R.brick_off) * kc;
+    const int ncell = blk.z * kc;
+    const int first = R.cell_off + (blk.y - R.brick_off) * kc;
     const int base = C.start[first];
-    const int cnt = C.start[first + kc] - base;
-    // shared layout: rcount sst[kc+1] cbase[kc] ccnt[kc] | q[cap] p[cap] e[cap] |
-    //                rs[rcap] rt[rcap] rw[rcap] rg[3 rcap]
-    int& rcount = *(int*)smem;
-    int* sst = (int*)smem + 1;
-    int* cbase = sst + (kc + 1);
-    int* ccnt = cbase + kc;
-    size_t off = ((size_t)(3 * kc + 2) * sizeof(int) + 31) & ~(size_t)31;
-    vec* sq = (vec*)(smem + off);
-    vec* sp = sq + cap;
-    E* se = (E*)(sp + cap);
-    unsigned char* rb = (unsigned char*)(se + cap);
-    rb = (unsigned char*)(((size_t)rb + 15) & ~(size_t)15);
-    int* rs = (int*)rb;
-    int* rt = rs + rcap;
-    T* rw = (T*)(rt + rcap);
-    T* rg = rw + rcap;
-    const bool in_smem = cnt <= cap;
-    for (int c = threadIdx.x; c <= kc; c += blockDim.x) sst[c] = C.start[first + c] - base;
-    vec* q = in_smem ? sq : C.qB + base;
-    vec* p = in_smem ? sp : C.pB + base;
-    E* e = in_smem ? se : C.eB + base;
+    const int cnt = C.start[first + ncell] - base;
+    // shared layout: sst[ccap+1] | px py pz [pcap] | e[pcap] | cur[pcap]
+    unsigned char* sm = (unsigned char*)(((size_t)smem_raw + 15) & ~(size_t)15);
+    int* sst = (int*)sm;
+    T* px = (T*)(sm + (((size_t)(ccap + 1) * sizeof(int) + 15) & ~(size_t)15));
+    T* py = px + pcap;
+    T* pz = py + pcap;
+    E* se = (E*)((((size_t)(pz + pcap)) + 7) & ~(size_t)7);
+    unsigned char* cur = (unsigned char*)(se + pcap);
+    const bool in_smem = cnt <= pcap;
+    for (int c = threadIdx.x; c <= ncell; c += blockDim.x) sst[c] = C.start[first + c] - base;
     if (in_smem)
         for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
-            sq[s] = C.qB[base + s];
-            sp[s] = C.pB[base + s];
+            const vec pv = C.pB[base + s];
+            px[s] = pv.x; py[s] = pv.y; pz[s] = pv.z;
             se[s] = C.eB[base + s];
+            cur[s] = 0;
         }
-    if (threadIdx.x == 0) rcount = 0;
+    draw_forward_gaussians(C, base, base + cnt, (uint32_t)rep);
     __syncthreads();
-    const uint32_t step = (uint32_t)*C.step;
-    const T lx = cell_len<T>(R, 0), ly = cell_len<T>(R, 1), lz = cell_len<T>(R, 2);
     const int Bx = R.B[0], By = R.B[1], Bz = R.B[2];
+    const size_t capn = (size_t)C.N;   // stride of the entry-major forward list
     for (int di = 0; di < 14; ++di) {
-        const int dxo = c_dirs[di][0], dyo = c_dirs[di][1], dzo = c_dirs[di][2];
+        const int dyo = c_dirs[di][1], dzo = c_dirs[di][2];
         const int lead = dzo != 0 ? 2 : (dyo != 0 ? 1 : 0);
         const int klead = lead == 2 ? kz : (lead == 1 ? ky : kx);
         const int Blead = lead == 2 ? Bz : (lead == 1 ? By : Bx);
         const bool odd = (Blead == 1) && (klead & 1);
-        // the (0,0,0) round is split in two halves by x parity: its cell
-        // pairs are all disjoint, so any split keeps the sequence's meaning
-        const int ncol = di == 0 ? 2 : (odd ? 3 : 2);
-        const T sx = shift<T>(dxo, lx), sy = shift<T>(dyo, ly), sz = shift<T>(dzo, lz);
+        const int ncol = di == 0 ? 1 : (odd ? 3 : 2);
         for (int col = 0; col < ncol; ++col) {
-            // (a) enumerate the round's pairs
-            for (int c = threadIdx.x; c < kc; c += blockDim.x) {
-                ccnt[c] = 0;
-                const int lxc = c % kx, lyc = (c / kx) % ky, lzc = c / (kx * ky);
+            for (int cg = threadIdx.x; cg < ncell; cg += blockDim.x) {
                 if (di > 0) {
+                    const int c = cg % kc;
+                    const int lxc = c % kx, lyc = (c / kx) % ky, lzc = c / (kx * ky);
                     const int ll = lead == 2 ? lzc : (lead == 1 ? lyc : lxc);
                     const int my = (odd && ll == klead - 1) ? 2 : (ll & 1);
                     if (my != col) continue;
-                } else if ((lxc & 1) != col) {
-                    continue;
                 }
-                int nx = lxc + dxo, ny = lyc + dyo, nz = lzc + dzo;
-                if (Bx == 1) nx = nx < 0 ? nx + kx : (nx >= kx ? nx - kx : nx);
-                else if (nx < 0 || nx >= kx) continue;
-                if (By == 1) ny = ny < 0 ? ny + ky : (ny >= ky ? ny - ky : ny);
-                else if (ny < 0 || ny >= ky) continue;
-                if (Bz == 1) nz = nz < 0 ? nz + kz : (nz >= kz ? nz - kz : nz);
-                else if (nz < 0 || nz >= kz) continue;
-                const int c1 = (nz * ky + ny) * kx + nx;
-                const int e0 = sst[c + 1], e1 = sst[c1 + 1];
-                int k = 0;
-                for (int s = sst[c]; s < e0; ++s) {
-                    const vec qs = q[s];
-                    for (int t = (di == 0) ? s + 1 : sst[c1]; t < e1; ++t) {
-                        const vec qt = q[t];
-                        const T dx = (qs.x - qt.x) - sx, dy = (qs.y - qt.y) - sy, dz = (qs.z - qt.z) - sz;
-                        k += (dx * dx + dy * dy + dz * dz < C.rc2) ? 1 : 0;
-                    }
-                }
-                if (k == 0) continue;
-                const int b = atomicAdd(&rcount, k);
-                cbase[c] = b;
-                ccnt[c] = (b + k <= rcap) ? k : -1;   // -1: redo inline in (c)
-                if (b + k > rcap) {
-                    // reserved slots below rcap stay unused: mark them
-                    for (int m = b; m < rcap; ++m) rs[m] = -1;
-                    continue;
-                }
-                int m = b;
-                for (int s = sst[c]; s < e0; ++s) {
-                    const vec qs = q[s];
-                    for (int t = (di == 0) ? s + 1 : sst[c1]; t < e1; ++t) {
-                        const vec qt = q[t];
-                        const T dx = (qs.x - qt.x) - sx, dy = (qs.y - qt.y) - sy, dz = (qs.z - qt.z) - sz;
-                        const T r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < C.rc2) {
-                            rs[m] = s;
-                            rt[m] = t;
-                            rw[m] = T(1) - tsqrt(r2) * C.inv_rc;
-                            ++m;
+                const int e0 = sst[cg + 1];
+                for (int s = sst[cg]; s < e0; ++s) {
+                    const int nf = C.fwd_n[base + s];
+                    int m = in_smem ? cur[s] : C.fwd_cur[base + s];
+                    for (; m < nf; ++m) {
+                        const size_t at = (size_t)m * capn + base + s;
+                        const int packed = C.fwd_j[at];
+                        if ((packed >> NBR_J_BITS) != di) break;
+                        const int t = (packed & NBR_J_MASK) - base;
+                        vec gw = C.fwd_g[at];
+                        gw.w = C.fwd_w[at];
+                        // the pair map of Eq. (SSA_ij) at fixed gamma_st (as in ssa_apply)
+                        T psx, psy, psz, ptx, pty, ptz;
+                        E es, et;
+                        if (in_smem) {
+                            psx = px[s]; psy = py[s]; psz = pz[s];
+                            ptx = px[t]; pty = py[t]; ptz = pz[t];
+                            es = se[s]; et = se[t];
+                        } else {
+                            const vec a = C.pB[base + s], b = C.pB[base + t];
+                            psx = a.x; psy = a.y; psz = a.z; ptx = b.x; pty = b.y; ptz = b.z;
+                            es = C.eB[base + s]; et = C.eB[base + t];
+                        }
+                        const T w = gw.w;
+                        const T chi = w * w;
+                        const T gam = C.sig2_4 * (beta_of(es, R) + beta_of(et, R));
+                        const T aa = T(2) * gam * chi * dt * C.inv_m;
+                        const T amp = (gam != T(0)) ? C.sigma * tsqrt(C.m * (-texpm1(T(-2) * aa)) / gam)
+                                                    : T(2) * C.sigma * w * sqrt_dt;
+                        const T em1 = texpm1(-aa);
+                        const T Dx = T(0.5) * (em1 * (psx - ptx) + amp * gw.x);
+                        const T Dy = T(0.5) * (em1 * (psy - pty) + amp * gw.y);
+                        const T Dz = T(0.5) * (em1 * (psz - ptz) + amp * gw.z);
+                        const T snx = psx + Dx, sny = psy + Dy, snz = psz + Dz;
+                        const T tnx = ptx - Dx, tny = pty - Dy, tnz = ptz - Dz;
+                        const T dK = ((snx - psx) * (snx + psx) + (sny - psy) * (sny + psy) +
+                                      (snz - psz) * (snz + psz) + (tnx - ptx) * (tnx + ptx) +
+                                      (tny - pty) * (tny + pty) + (tnz - ptz) * (tnz + ptz)) *
+                                     (T(0.25) * C.inv_m);
+                        if (in_smem) {
+                            px[s] = snx; py[s] = sny; pz[s] = snz;
+                            px[t] = tnx; py[t] = tny; pz[t] = tnz;
+                            se[s] = eps_add(es, -dK);
+                            se[t] = eps_add(et, -dK);
+                        } else {
+                            vec a = C.pB[base + s], b = C.pB[base + t];
+                            a.x = snx; a.y = sny; a.z = snz;
+                            b.x = tnx; b.y = tny; b.z = tnz;
+                            C.pB[base + s] = a;
+                            C.pB[base + t] = b;
+                            C.eB[base + s] = eps_add(es, -dK);
+                            C.eB[base + t] = eps_add(et, -dK);
                         }
                     }
+                    if (in_smem) cur[s] = (unsigned char)m;
+                    else C.fwd_cur[base + s] = m;
                 }
             }
-            __syncthreads();
-            // (b) Gaussians of the buffered pairs
-            const int nr = min(rcount, rcap);
-            for (int m = threadIdx.x; m < nr; m += blockDim.x) {
-                const int s = rs[m], t = rt[m];
-                if (s < 0 || s >= cnt || t < 0 || t >= cnt) continue;
-                const T3<T> G = pair_gauss<T>(C.seed, step, (uint32_t)rep, id_of(q[s]), id_of(q[t]));
-                rg[3 * m] = G.x;
-                rg[3 * m + 1] = G.y;
-                rg[3 * m + 2] = G.z;
-            }
-            __syncthreads();
-            // (c) the pair maps, in sequence order within each cell pair
-            for (int c = threadIdx.x; c < kc; c += blockDim.x) {
-                const int k = ccnt[c];
-                if (k > 0) {
-                    for (int m = cbase[c]; m < cbase[c] + k; ++m)
-                        ssa_apply(C, R, p, e, rs[m], rt[m], rw[m], T3<T>{rg[3 * m], rg[3 * m + 1], rg[3 * m + 2]},
-                                  dt, sqrt_dt);
-                } else if (k < 0) {
-                    const int lxc = c % kx, lyc = (c / kx) % ky, lzc = c / (kx * ky);
-                    int nx = lxc + dxo, ny = lyc + dyo, nz = lzc + dzo;
-                    nx = nx < 0 ? nx + kx : (nx >= kx ? nx - kx : nx);
-                    ny = ny < 0 ? ny + ky : (ny >= ky ? ny - ky : ny);
-                    nz = nz < 0 ? nz + kz : (nz >= kz ? nz - kz : nz);
-                    const int c1 = (nz * ky + ny) * kx + nx;
-                    const int e0 = sst[c + 1], e1 = sst[c1 + 1];
-                    for (int s = sst[c]; s < e0; ++s) {
-                        const vec qs = q[s];
-                        for (int t = (di == 0) ? s + 1 : sst[c1]; t < e1; ++t) {
-                            const vec qt = q[t];
-                            const T dx = (qs.x - qt.x) - sx, dy = (qs.y - qt.y) - sy, dz = (qs.z - qt.z) - sz;
-                            const T r2 = dx * dx + dy * dy + dz * dz;
-                            if (r2 < C.rc2)
-                                ssa_pair(C, R, (uint32_t)rep, step, p, e, s, t, id_of(qs), id_of(qt), r2, dt,
-                                         sqrt_dt);
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) rcount = 0;
             __syncthreads();
         }
     }
     for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
-        vec pv = p[s];
-        pv.w = beta_of(e[s], R);
+        vec pv = C.pB[base + s];
+        if (in_smem) {
+            pv.x = px[s]; pv.y = py[s]; pv.z = pz[s];
+            C.eB[base + s] = se[s];
+        }
+        pv.w = beta_of(C.eB[base + s], R);
         C.pB[base + s] = pv;
-        if (in_smem) C.eB[base + s] = e[s];
     }
 }
 
-// Whole-replica SSA (the DPDE_SSA scheme): one launch per (direction, colour)
-// round over every cell of every replica, updating set B in place.
+// Gaussians for the whole-replica SSA scheme (its rounds are separate launches).
 template <class T>
-__global__ void k_ssa_round(Ctx<T> C, int di, int col, T dt, T sqrt_dt) {
-    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t0 >= C.ncells) return;
-    const int rep = C.rep_of_cell[t0];
-    const RepInfo& R = C.reps[rep];
-    const int lc = t0 - R.cell_off;   // z-major enumeration of the replica's cells
-    const int cc[3] = {lc % R.nc[0], (lc / R.nc[0]) % R.nc[1], lc / (R.nc[0] * R.nc[1])};
-    const int* del = c_dirs[di];
-    const int lead = del[2] != 0 ? 2 : (del[1] != 0 ? 1 : 0);
-    if (di > 0) {
-        const bool odd = R.nc[lead] & 1;
-        const int ll = cc[lead];
-        const int my = (odd && ll == R.nc[lead] - 1) ? 2 : (ll & 1);
-        if (my != col) return;
-    }
-    int nb[3];
-    for (int d = 0; d < 3; ++d) {
-        int ln = cc[d] + del[d];
-        nb[d] = ln < 0 ? ln + R.nc[d] : (ln >= R.nc[d] ? ln - R.nc[d] : ln);
-    }
-    const int c = cell_index(C.tab, R, cc[0], cc[1], cc[2]);
-    const int c1 = cell_index(C.tab, R, nb[0], nb[1], nb[2]);
-    const T sx = shift<T>(del[0], cell_len<T>(R, 0));
-    const T sy = shift<T>(del[1], cell_len<T>(R, 1));
-    const T sz = shift<T>(del[2], cell_len<T>(R, 2));
+__global__ void k_fwd_gauss(Ctx<T> C) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= C.N) return;
+    const int nf = C.fwd_n[s];
+    const uint32_t ids = C.idB[s];
+    const uint32_t rep = (uint32_t)C.rep_of_slot[s];
     const uint32_t step = (uint32_t)*C.step;
-    const int e0 = C.start[c + 1], e1 = C.start[c1 + 1];
-    for (int s = C.start[c]; s < e0; ++s) {
-        const vec_t<T> qs = C.qB[s];
-        for (int t = (di == 0) ? s + 1 : C.start[c1]; t < e1; ++t) {
-            const vec_t<T> qt = C.qB[t];
-            const T dx = (qs.x - qt.x) - sx;
-            const T dy = (qs.y - qt.y) - sy;
-            const T dz = (qs.z - qt.z) - sz;
-            const T r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 < C.rc2)
-                ssa_pair(C, R, (uint32_t)rep, step, C.pB, C.eB, s, t, id_of(qs), id_of(qt), r2, dt, sqrt_dt);
-        }
+    for (int m = 0; m < nf; ++m) {
+        const size_t at = (size_t)m * C.N + s;
+        const int t = C.fwd_j[at] & NBR_J_MASK;
+        const T3<T> G = pair_gauss<T>(C.seed, step, rep, ids, C.idB[t]);
+        vec_t<T> g;
+        g.x = G.x; g.y = G.y; g.z = G.z; g.w = T(0);
+        C.fwd_g[at] = g;
     }
+}
+
+template <class T>
+__global__ void k_refresh_beta(Ctx<T> C) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= C.N) return;
+    C.pB[s].w = beta_of(C.eB[s], C.reps[C.rep_of_slot[s]]);
 }
 
 __global__ void k_step_inc(long long* step) { *step += 1; }
