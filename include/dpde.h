@@ -259,6 +259,44 @@ int dpde_destroy(dpde_handle* h);
  * is NULL). Never NULL; valid until the next call on the same handle. */
 const char* dpde_last_error(const dpde_handle* h);
 
+/* ---- observables without device allocation ---- */
+
+/* Fixed limits of dpde_observables_noalloc (its scratch is one file-scope
+ * device array of DPDE_NOALLOC_SCRATCH_BYTES = 4,217,344 bytes, about 4 MiB,
+ * that every GPU which loads the library holds until the process exits). */
+#define DPDE_NOALLOC_MAX_N            262144
+#define DPDE_NOALLOC_MAX_CELLS        262144
+#define DPDE_NOALLOC_SCRATCH_BYTES    4217344ull
+
+/* Observables of one system (the quantities of dpde_observables, computed
+ * in double) from a state the caller holds in device memory, without any
+ * device allocation -- for callers that cannot call cudaMalloc: code that
+ * runs while a stream is being captured into a CUDA graph, plug-ins inside
+ * a host framework that owns all device memory, processes under a hard
+ * device-memory cap. The paper has no counterpart; this is a service entry
+ * point of the library, not part of the method.
+ *  params  : m, r_cut, a of the system (sigma, seed, precision unused).
+ *  replica : n <= DPDE_NOALLOC_MAX_N, box with floor(L_d / r_cut) >= 3 and
+ *            prod_d floor(L_d / r_cut) <= DPDE_NOALLOC_MAX_CELLS, C_v
+ *            (bricks unused). Larger systems: DPDE_ERR_ARG with a message
+ *            from dpde_noalloc_last_error().
+ *  q, p    : 3n doubles each, eps: n doubles -- DEVICE pointers (read only).
+ *  stream  : cudaStream_t to run on (NULL = legacy default stream).
+ *  out     : one dpde_obs, host memory (out->step is 0).
+ * All working memory is the library's fixed device scratch array; the call
+ * clears the parts that must start at zero. The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) once for that device:
+ * make it before any stream capture. Every call shares the array, so calls
+ * whose work overlaps on a GPU race; callers serialise them. Synchronous on
+ * `stream`. Returns DPDE_ERR_NEG_EPS / DPDE_ERR_NONFINITE like
+ * dpde_observables (out is still filled). */
+int dpde_observables_noalloc(const dpde_params* params, const dpde_replica* replica,
+                             const double* q, const double* p, const double* eps,
+                             void* stream, dpde_obs* out);
+
+/* Message of the last failed dpde_observables_noalloc call of this thread. */
+const char* dpde_noalloc_last_error(void);
+
 /* ---- diagnostics ---- */
 
 /* Phases of one step, for dpde_step_profiled. */

@@ -64,7 +64,7 @@ _lib = None
 EXPORTS = ["dpde_create", "dpde_set_state", "dpde_get_state", "dpde_step", "dpde_sync",
            "dpde_observables", "dpde_get_step", "dpde_destroy", "dpde_last_error",
            "dpde_debug_philox", "dpde_debug_gaussian", "dpde_step_profiled", "dpde_get_cells",
-           "dpde_checkpoint", "dpde_restore"]
+           "dpde_checkpoint", "dpde_restore", "dpde_observables_noalloc", "dpde_noalloc_last_error"]
 PHASES = ["kick_drift", "scan", "gather", "force", "ssa", "sweep1", "sweep2", "other"]
 
 
@@ -89,6 +89,10 @@ def lib():
         L.dpde_destroy.argtypes = [vp]
         L.dpde_last_error.argtypes = [vp]
         L.dpde_last_error.restype = C.c_char_p
+        L.dpde_observables_noalloc.argtypes = [C.POINTER(dpde_params), C.POINTER(dpde_replica), vp, vp, vp,
+                                               vp, C.POINTER(dpde_obs)]
+        L.dpde_noalloc_last_error.argtypes = []
+        L.dpde_noalloc_last_error.restype = C.c_char_p
         L.dpde_checkpoint.argtypes = [vp, vp, C.POINTER(C.c_uint64)]
         L.dpde_restore.argtypes = [vp, vp, C.c_uint64]
         L.dpde_get_cells.argtypes = [vp, C.POINTER(C.c_int32)]
@@ -154,6 +158,17 @@ def dpde_observables(h, n_replicas):
     out = (dpde_obs * n_replicas)()
     rc = lib().dpde_observables(h, out)
     return rc, [o.as_dict() for o in out]
+
+
+def dpde_observables_noalloc(params: dpde_params, replica: dpde_replica, q, p, eps, stream=None):
+    """Observables of one system from device arrays (torch CUDA tensors or raw
+    device pointers), computed without any device allocation."""
+    out = dpde_obs()
+    rc = lib().dpde_observables_noalloc(C.byref(params), C.byref(replica), _addr(q), _addr(p), _addr(eps),
+                                        C.c_void_p(stream) if stream else None, C.byref(out))
+    if rc not in (DPDE_OK, DPDE_ERR_NEG_EPS, DPDE_ERR_NONFINITE):
+        raise DPDEError(rc, lib().dpde_noalloc_last_error().decode())
+    return rc, out.as_dict()
 
 
 def dpde_destroy(h):
