@@ -51,6 +51,9 @@ struct dpde_handle {
     void *eA = nullptr, *eB = nullptr, *nbr_w = nullptr, *fwd_g = nullptr, *fwd_w = nullptr;
     int *cA = nullptr, *cB = nullptr, *nbr_j = nullptr, *nbr_n = nullptr, *fwd_j = nullptr, *fwd_n = nullptr;
     int* fwd_cur = nullptr;
+    uint32_t* ssa_ent = nullptr;
+    void* ssa_gw = nullptr;
+    int* ssa_off = nullptr;
     int4 *tile_org = nullptr, *tile_dim = nullptr;
     int ntiles = 0;
     int kc_max = 1;
@@ -112,6 +115,7 @@ Ctx<T> make_ctx(dpde_handle* h) {
     C.count = h->cnt; C.fill = h->cnt + h->ncells; C.start = h->start;
     C.nbr_j = h->nbr_j; C.nbr_w = (T*)h->nbr_w; C.nbr_n = h->nbr_n; C.nbr_cap = h->nbr_cap;
     C.fwd_j = h->fwd_j; C.fwd_g = (vec_t<T>*)h->fwd_g; C.fwd_w = (T*)h->fwd_w; C.fwd_n = h->fwd_n; C.fwd_cur = h->fwd_cur;
+    C.ssa_ent = h->ssa_ent; C.ssa_gw = (vec_t<T>*)h->ssa_gw; C.ssa_off = h->ssa_off;
     C.rep_of_slot = h->rep_of_slot; C.rep_of_cell = h->rep_of_cell;
     C.brick_rep = h->brick_rep; C.tab = h->tab;
     C.reps = h->d_reps; C.step = h->d_step; C.status = h->d_status;
@@ -255,7 +259,7 @@ void free_all(dpde_handle* h) {
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
     void* bufs[] = {h->qA, h->pA, h->qB, h->pB, h->F, h->dp, h->eA, h->eB, h->nbr_w, h->cA, h->cB, h->nbr_j,
-                    h->nbr_n, h->fwd_j, h->fwd_g, h->fwd_w, h->fwd_n, h->fwd_cur, h->tile_org, h->tile_dim, h->ssa_blocks, h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
+                    h->nbr_n, h->fwd_j, h->fwd_g, h->fwd_w, h->fwd_n, h->fwd_cur, h->tile_org, h->tile_dim, h->ssa_blocks, h->ssa_ent, h->ssa_gw, h->ssa_off, h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
                     h->rep_of_cell, h->brick_rep, h->tab, h->chunk_rep, h->chunk_begin, h->chunk_end,
                     h->rep_chunk_begin, h->partial, h->obs_out, h->d_reps, h->d_step, h->d_status,
                     h->staging, h->cells_out};
@@ -515,6 +519,9 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         CKC(cudaMemset(h->fwd_cur, 0, sizeof(int) * n1));
     }
     CKC(cudaMalloc(&h->ssa_blocks, sizeof(int4) * sblk.size()));
+    CKC(cudaMalloc(&h->ssa_ent, sizeof(uint32_t) * n1 * SSA_ENT_PER_SLOT));
+    CKC(cudaMalloc(&h->ssa_gw, vsz * n1 * SSA_ENT_PER_SLOT));
+    CKC(cudaMalloc(&h->ssa_off, sizeof(int) * 14 * (c1 + sblk.size())));
     CKC(cudaMemcpy(h->ssa_blocks, sblk.data(), sizeof(int4) * sblk.size(), cudaMemcpyHostToDevice));
     if (h->mixed)
         CKC(cudaFuncSetAttribute(k_ssa_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ssa_smem));

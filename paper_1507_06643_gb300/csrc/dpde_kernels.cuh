@@ -35,6 +35,9 @@ template <class T> struct Ctx {
     vec* fwd_g;      //   G_it of each entry (x, y, z)
     int* fwd_n;
     int* fwd_cur;    // SSA cursor into each forward list
+    uint32_t* ssa_ent;   // Hybrid SSA buckets: s | t << 16 (block-local slots),
+    vec* ssa_gw;         //   (G, w), per block region [first slot * SSA_ENT_PER_SLOT ...)
+    int* ssa_off;        //   chain offsets, 14 per cell (+14 per block)
     const int* rep_of_slot;
     const int* rep_of_cell;
     const int* brick_rep;
@@ -865,37 +868,52 @@ __global__ void k_ssa_round(Ctx<T> C, int di, int col, int whole_box, T dt, T sq
     }
 }
 
-// Gaussians of the forward entries of particles [s0, s1) (state
-// independent: drawn ahead of the sequential SSA rounds, all lanes busy).
-template <class T>
-__device__ __forceinline__ void draw_forward_gaussians(const Ctx<T>& C, int s0, int s1, uint32_t rep) {
-    const uint32_t step = (uint32_t)*C.step;
-    const size_t N = (size_t)C.N;
-    for (int s = s0 + (int)threadIdx.x; s < s1; s += blockDim.x) {
-        const int nf = C.fwd_n[s];
-        const uint32_t ids = C.idB[s];
-        for (int m = 0; m < nf; ++m) {
-            const size_t at = (size_t)m * N + s;
-            const int t = C.fwd_j[at] & NBR_J_MASK;
-            const T3<T> G = pair_gauss<T>(C.seed, step, rep, ids, C.idB[t]);
-            vec_t<T> g;
-            g.x = G.x; g.y = G.y; g.z = G.z; g.w = T(0);
-            C.fwd_g[at] = g;
-        }
-    }
-}
-
 // Hybrid's SSA over set A. A block owns a run of consecutive domains
 // ("bricks") of one replica -- a contiguous slot range in brick-major cell
 // order -- so that every round has thousands of independent cell pairs
-// between two barriers. Momenta (as x, y, z arrays) and internal energies
-// are staged in shared memory when they fit (else the block works on
-// global memory in place). After the Gaussians are drawn, the rounds
-// (direction di, colour col) run: each thread takes cell pairs
-// (c, c + delta_di) of colour col and applies, in sequence order, the
-// direction-di forward entries of c's particles. Writes set B back with
-// beta refreshed.
+// between two barriers. Momenta (x, y, z arrays) and internal energies are
+// staged in shared memory when they fit (else the block works on global
+// memory in place).
+// Prologue: each thread owns a contiguous run of cells; it counts its
+// particles' forward entries per direction, 14 block scans place them, and
+// the thread writes every entry (s, t, G, w) into its direction's bucket in
+// sequence order -- drawing the Gaussians with all lanes busy -- together
+// with each cell's chain offsets. Rounds (direction di, colour col): each
+// thread takes cell pairs (c, c + delta_di) of colour col and applies the
+// chain of c from the di bucket, in order. Writes set B back with beta
+// refreshed. Blocks whose entries exceed their bucket region run the chains
+// directly from the forward lists with inline Gaussians.
 constexpr int SSA_THREADS = 1024;
+constexpr int SSA_ENT_PER_SLOT = 12;   // bucket capacity per particle (mean ~5.4 at density 3)
+
+template <class T>
+__device__ __forceinline__ void ssa_map_smem(const Ctx<T>& C, const RepInfo& R, T* px, T* py, T* pz,
+                                             eps_t<T>* se, int s, int t, const vec_t<T>& gw, T dt,
+                                             T sqrt_dt) {
+    // the pair map of Eq. (SSA_ij) at fixed gamma_st (as in ssa_apply)
+    const T psx = px[s], psy = py[s], psz = pz[s];
+    const T ptx = px[t], pty = py[t], ptz = pz[t];
+    const eps_t<T> es = se[s], et = se[t];
+    const T w = gw.w;
+    const T chi = w * w;
+    const T gam = C.sig2_4 * (beta_of(es, R) + beta_of(et, R));
+    const T aa = T(2) * gam * chi * dt * C.inv_m;
+    const T amp = (gam != T(0)) ? C.sigma * tsqrt(C.m * (-texpm1(T(-2) * aa)) / gam)
+                                : T(2) * C.sigma * w * sqrt_dt;
+    const T em1 = texpm1(-aa);
+    const T Dx = T(0.5) * (em1 * (psx - ptx) + amp * gw.x);
+    const T Dy = T(0.5) * (em1 * (psy - pty) + amp * gw.y);
+    const T Dz = T(0.5) * (em1 * (psz - ptz) + amp * gw.z);
+    const T snx = psx + Dx, sny = psy + Dy, snz = psz + Dz;
+    const T tnx = ptx - Dx, tny = pty - Dy, tnz = ptz - Dz;
+    const T dK = ((snx - psx) * (snx + psx) + (sny - psy) * (sny + psy) + (snz - psz) * (snz + psz) +
+                  (tnx - ptx) * (tnx + ptx) + (tny - pty) * (tny + pty) + (tnz - ptz) * (tnz + ptz)) *
+                 (T(0.25) * C.inv_m);
+    px[s] = snx; py[s] = sny; pz[s] = snz;
+    px[t] = tnx; py[t] = tny; pz[t] = tnz;
+    se[s] = eps_add(es, -dK);
+    se[t] = eps_add(et, -dK);
+}
 
 template <class T>
 __global__ void __launch_bounds__(SSA_THREADS) k_ssa_block(Ctx<T> C, const int4* __restrict__ blocks, T dt,
@@ -912,14 +930,16 @@ __global__ void __launch_bounds__(SSA_THREADS) k_ssa_block(Ctx<T> C, const int4*
     const int first = R.cell_off + (blk.y - R.brick_off) * kc;
     const int base = C.start[first];
     const int cnt = C.start[first + ncell] - base;
-    // shared layout: sst[ccap+1] | px py pz [pcap] | e[pcap] | cur[pcap]
+    const size_t N = (size_t)C.N;
+    // shared layout: sst[ccap+1] | px py pz [pcap] | e[pcap] ; small arrays below
     unsigned char* sm = (unsigned char*)(((size_t)smem_raw + 15) & ~(size_t)15);
     int* sst = (int*)sm;
     T* px = (T*)(sm + (((size_t)(ccap + 1) * sizeof(int) + 15) & ~(size_t)15));
     T* py = px + pcap;
     T* pz = py + pcap;
     E* se = (E*)((((size_t)(pz + pcap)) + 7) & ~(size_t)7);
-    unsigned char* cur = (unsigned char*)(se + pcap);
+    __shared__ int bbase[15];
+    __shared__ int scan_sh[32];
     const bool in_smem = cnt <= pcap;
     for (int c = threadIdx.x; c <= ncell; c += blockDim.x) sst[c] = C.start[first + c] - base;
     if (in_smem)
@@ -927,12 +947,68 @@ __global__ void __launch_bounds__(SSA_THREADS) k_ssa_block(Ctx<T> C, const int4*
             const vec pv = C.pB[base + s];
             px[s] = pv.x; py[s] = pv.y; pz[s] = pv.z;
             se[s] = C.eB[base + s];
-            cur[s] = 0;
         }
-    draw_forward_gaussians(C, base, base + cnt, (uint32_t)rep);
     __syncthreads();
+    // --- prologue: bucket the forward entries by direction ---
+    const int cpt = (ncell + SSA_THREADS - 1) / SSA_THREADS;
+    const int c0 = min(ncell, (int)threadIdx.x * cpt), c1 = min(ncell, c0 + cpt);
+    int run[14];
+#pragma unroll
+    for (int d = 0; d < 14; ++d) run[d] = 0;
+    for (int s = sst[c0]; s < sst[c1]; ++s) {
+        const int nf = C.fwd_n[base + s];
+        for (int m = 0; m < nf; ++m) {
+            const int d = C.fwd_j[(size_t)m * N + base + s] >> NBR_J_BITS;
+#pragma unroll
+            for (int dd = 0; dd < 14; ++dd) run[dd] += (dd == d) ? 1 : 0;
+        }
+    }
+    int total = 0;
+#pragma unroll
+    for (int d = 0; d < 14; ++d) {
+        int tot;
+        const int ex = block_exclusive_scan(run[d], scan_sh, tot);
+        run[d] = ex;
+        if (threadIdx.x == 0) bbase[d] = total;
+        total += tot;
+    }
+    if (threadIdx.x == 0) bbase[14] = total;
+    const size_t ebase = (size_t)base * SSA_ENT_PER_SLOT;   // this block's bucket region
+    const bool bucketed = in_smem && total <= cnt * SSA_ENT_PER_SLOT;   // uniform
+    int* off = C.ssa_off + (size_t)(first + blockIdx.x) * 14;
+    __syncthreads();
+    if (bucketed) {
+        const uint32_t step = (uint32_t)*C.step;
+        for (int c = c0; c < c1; ++c) {
+#pragma unroll
+            for (int d = 0; d < 14; ++d) off[(size_t)c * 14 + d] = bbase[d] + run[d];
+            for (int s = sst[c]; s < sst[c + 1]; ++s) {
+                const int nf = C.fwd_n[base + s];
+                const uint32_t ids = C.idB[base + s];
+                for (int m = 0; m < nf; ++m) {
+                    const size_t at = (size_t)m * N + base + s;
+                    const int packed = C.fwd_j[at];
+                    const int d = packed >> NBR_J_BITS;
+                    const int t = (packed & NBR_J_MASK) - base;
+                    int pos = 0;
+#pragma unroll
+                    for (int dd = 0; dd < 14; ++dd)
+                        if (dd == d) pos = bbase[dd] + run[dd]++;
+                    const T3<T> G = pair_gauss<T>(C.seed, step, (uint32_t)rep, ids, C.idB[base + t]);
+                    vec gw;
+                    gw.x = G.x; gw.y = G.y; gw.z = G.z; gw.w = C.fwd_w[at];
+                    C.ssa_ent[ebase + pos] = (uint32_t)s | ((uint32_t)t << 16);
+                    C.ssa_gw[ebase + pos] = gw;
+                }
+            }
+        }
+        if (threadIdx.x == 0)
+            for (int d = 0; d < 14; ++d) off[(size_t)ncell * 14 + d] = bbase[d + 1];
+    }
+    __syncthreads();
+    // --- rounds ---
     const int Bx = R.B[0], By = R.B[1], Bz = R.B[2];
-    const size_t capn = (size_t)C.N;   // stride of the entry-major forward list
+    const uint32_t step = (uint32_t)*C.step;
     for (int di = 0; di < 14; ++di) {
         const int dyo = c_dirs[di][1], dzo = c_dirs[di][2];
         const int lead = dzo != 0 ? 2 : (dyo != 0 ? 1 : 0);
@@ -949,62 +1025,29 @@ __global__ void __launch_bounds__(SSA_THREADS) k_ssa_block(Ctx<T> C, const int4*
                     const int my = (odd && ll == klead - 1) ? 2 : (ll & 1);
                     if (my != col) continue;
                 }
-                const int e0 = sst[cg + 1];
-                for (int s = sst[cg]; s < e0; ++s) {
-                    const int nf = C.fwd_n[base + s];
-                    int m = in_smem ? cur[s] : C.fwd_cur[base + s];
-                    for (; m < nf; ++m) {
-                        const size_t at = (size_t)m * capn + base + s;
-                        const int packed = C.fwd_j[at];
-                        if ((packed >> NBR_J_BITS) != di) break;
-                        const int t = (packed & NBR_J_MASK) - base;
-                        vec gw = C.fwd_g[at];
-                        gw.w = C.fwd_w[at];
-                        // the pair map of Eq. (SSA_ij) at fixed gamma_st (as in ssa_apply)
-                        T psx, psy, psz, ptx, pty, ptz;
-                        E es, et;
-                        if (in_smem) {
-                            psx = px[s]; psy = py[s]; psz = pz[s];
-                            ptx = px[t]; pty = py[t]; ptz = pz[t];
-                            es = se[s]; et = se[t];
-                        } else {
-                            const vec a = C.pB[base + s], b = C.pB[base + t];
-                            psx = a.x; psy = a.y; psz = a.z; ptx = b.x; pty = b.y; ptz = b.z;
-                            es = C.eB[base + s]; et = C.eB[base + t];
-                        }
-                        const T w = gw.w;
-                        const T chi = w * w;
-                        const T gam = C.sig2_4 * (beta_of(es, R) + beta_of(et, R));
-                        const T aa = T(2) * gam * chi * dt * C.inv_m;
-                        const T amp = (gam != T(0)) ? C.sigma * tsqrt(C.m * (-texpm1(T(-2) * aa)) / gam)
-                                                    : T(2) * C.sigma * w * sqrt_dt;
-                        const T em1 = texpm1(-aa);
-                        const T Dx = T(0.5) * (em1 * (psx - ptx) + amp * gw.x);
-                        const T Dy = T(0.5) * (em1 * (psy - pty) + amp * gw.y);
-                        const T Dz = T(0.5) * (em1 * (psz - ptz) + amp * gw.z);
-                        const T snx = psx + Dx, sny = psy + Dy, snz = psz + Dz;
-                        const T tnx = ptx - Dx, tny = pty - Dy, tnz = ptz - Dz;
-                        const T dK = ((snx - psx) * (snx + psx) + (sny - psy) * (sny + psy) +
-                                      (snz - psz) * (snz + psz) + (tnx - ptx) * (tnx + ptx) +
-                                      (tny - pty) * (tny + pty) + (tnz - ptz) * (tnz + ptz)) *
-                                     (T(0.25) * C.inv_m);
-                        if (in_smem) {
-                            px[s] = snx; py[s] = sny; pz[s] = snz;
-                            px[t] = tnx; py[t] = tny; pz[t] = tnz;
-                            se[s] = eps_add(es, -dK);
-                            se[t] = eps_add(et, -dK);
-                        } else {
-                            vec a = C.pB[base + s], b = C.pB[base + t];
-                            a.x = snx; a.y = sny; a.z = snz;
-                            b.x = tnx; b.y = tny; b.z = tnz;
-                            C.pB[base + s] = a;
-                            C.pB[base + t] = b;
-                            C.eB[base + s] = eps_add(es, -dK);
-                            C.eB[base + t] = eps_add(et, -dK);
-                        }
+                if (bucketed) {
+                    const int m1 = off[(size_t)(cg + 1) * 14 + di];
+                    for (int m = off[(size_t)cg * 14 + di]; m < m1; ++m) {
+                        const uint32_t ent = C.ssa_ent[ebase + m];
+                        ssa_map_smem(C, R, px, py, pz, se, (int)(ent & 0xffffu), (int)(ent >> 16),
+                                     C.ssa_gw[ebase + m], dt, sqrt_dt);
                     }
-                    if (in_smem) cur[s] = (unsigned char)m;
-                    else C.fwd_cur[base + s] = m;
+                } else {
+                    // direct chains from the forward lists (global memory), inline Gaussians
+                    for (int s = C.start[first + cg] - base; s < C.start[first + cg + 1] - base; ++s) {
+                        const int nf = C.fwd_n[base + s];
+                        int m = C.fwd_cur[base + s];
+                        for (; m < nf; ++m) {
+                            const size_t at = (size_t)m * N + base + s;
+                            const int packed = C.fwd_j[at];
+                            if ((packed >> NBR_J_BITS) != di) break;
+                            const int t = packed & NBR_J_MASK;
+                            ssa_apply(C, R, C.pB, C.eB, base + s, t, C.fwd_w[at],
+                                      pair_gauss<T>(C.seed, step, (uint32_t)rep, C.idB[base + s], C.idB[t]), dt,
+                                      sqrt_dt);
+                        }
+                        C.fwd_cur[base + s] = m;
+                    }
                 }
             }
             __syncthreads();
@@ -1012,7 +1055,7 @@ __global__ void __launch_bounds__(SSA_THREADS) k_ssa_block(Ctx<T> C, const int4*
     }
     for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
         vec pv = C.pB[base + s];
-        if (in_smem) {
+        if (bucketed) {
             pv.x = px[s]; pv.y = py[s]; pv.z = pz[s];
             C.eB[base + s] = se[s];
         }
