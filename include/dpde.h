@@ -96,18 +96,18 @@
  *  The quotient ncell_d / L_d is formed once in double. A pair is "intra
  *  domain" (set A of Sec. III.B.2) iff both particles have the same brick.
  *  Order of the SSA sequence over A (the paper leaves it free, Sec. III.A.2):
- *   rounds over the 14 half-stencil directions delta in this order
- *     (0,0,0), (1,0,0), (-1,1,0), (0,1,0), (1,1,0), (-1,-1,1), (0,-1,1),
- *     (1,-1,1), (-1,0,1), (0,0,1), (1,0,1), (-1,1,1), (0,1,1), (1,1,1)
- *   (delta = (dx, dy, dz)); the leading axis of delta is z if dz != 0, else y
- *   if dy != 0, else x. Within direction delta, colours col = 0, 1, (2):
- *   col(c) = (local coordinate of c along the leading axis) mod 2, except
- *   that when the brick is periodic along that axis (B = 1) and k is odd the
- *   last local cell takes colour 2. Within (delta, col) the cell pairs
- *   (c, c + delta) (both in the same brick; the neighbour wraps only along
- *   periodic-brick axes) are disjoint and may be processed in any order. Within
- *   one cell pair, particles i of c (ascending id) outer, j of c + delta
- *   (ascending id) inner; for delta = 0, pairs i < j of c in that order.
+ *   the cells are coloured per axis by their local coordinate l in the brick,
+ *     col_d(l) = l mod 3, except that along an axis where the brick spans the
+ *     replica (B_d = 1, periodic) the last k_d mod 3 cells take colours 3, 4;
+ *   colours (col_z, col_y, col_x) are taken in lexicographic order (z major).
+ *   Cells of one colour have disjoint 3x3x3 neighbourhoods inside their
+ *   bricks and are processed in any order. Within a cell, its particles i in
+ *   ascending id, each applying its forward pairs (i, j) in the order
+ *   (segment, id_j): j lies in a neighbour cell of the same brick (wrapping
+ *   only along B_d = 1 axes) at offset (dx, dy, dz) with segment
+ *   9 (dz+1) + 3 (dy+1) + (dx+1) above 13, or in i's own cell (segment 13)
+ *   with id_j > id_i. DPDE_SSA uses the same order with the whole replica as
+ *   one brick (B = (1, 1, 1), k = ncell).
  *
  * ---------------------------------------------------------------------------
  * Precision modes
@@ -316,6 +316,13 @@ const char* dpde_noalloc_last_error(void);
  * not cleared). Synchronous. */
 int dpde_step_profiled(dpde_handle* h, int64_t n, double dt, int32_t scheme,
                        double* phase_ms);
+
+/* Number of kernel launches in one step of `scheme` (the kernel nodes of
+ * the step's CUDA graph, captured here without being run; *launches, host
+ * pointer). The count depends on the handle's geometry: the SSA part has one
+ * launch per non-empty cell colour class. No device work; the handle's state
+ * and step counter are unchanged. DPDE_ERR_ARG for a bad scheme. */
+int dpde_step_launches(dpde_handle* h, int32_t scheme, int64_t* launches);
 
 /* Cell coordinates (cx, cy, cz) of every particle in id order (3N int32,
  * host pointer), as the library binned them at the end of the last step.

@@ -411,15 +411,26 @@ static void ssa_pair(const fd_ctx* c, int64_t i, int64_t j)
     c->eps[j] -= 0.5 * dK;
 }
 
-/* The 14 half-stencil directions (dx, dy, dz) in SSA round order. */
-static const int ORA_DIRS[14][3] = {
-    {0, 0, 0},  {1, 0, 0},   {-1, 1, 0}, {0, 1, 0},  {1, 1, 0},
-    {-1, -1, 1}, {0, -1, 1}, {1, -1, 1}, {-1, 0, 1}, {0, 0, 1},
-    {1, 0, 1},  {-1, 1, 1},  {0, 1, 1},  {1, 1, 1}};
+/* Colour of a cell coordinate l along one axis of a domain with k cells:
+ * l mod 3, except that along a periodic domain axis (one domain spanning the
+ * replica) the trailing k mod 3 cells take colours 3 and 4, so that two
+ * cells of equal colour are at least 3 cells apart around the ring. */
+static int axis_colour(int l, int k, int periodic)
+{
+    int full = 3 * (k / 3);
+    if (periodic && l >= full) return 3 + (l - full);
+    return l % 3;
+}
 
-/* Enumerates the SSA sequence: visit(i, j) for each interacting intra-domain
- * pair, in the order the library header defines (rounds over directions and
- * colours; cell pairs of one round touch disjoint particles). */
+/* Enumerates the SSA sequence: visit(i, j) for each interacting pair of the
+ * domain (Hybrid's set A: same brick; or the whole replica when whole_box),
+ * in the order the library header defines: colours (cz, cy, cx) in
+ * lexicographic order (z major); within a colour the cells are independent
+ * (their 3x3x3 neighbourhoods are disjoint) and taken in any order; within a
+ * cell, particles i by ascending id, each applying its forward pairs -- the
+ * partners j in the 27 neighbour cells of the same domain whose cell offset
+ * segment 9 (dz+1) + 3 (dy+1) + (dx+1) exceeds 13, or equals 13 (same cell)
+ * with id_j > id_i -- ordered by (segment, id_j). */
 typedef void (*pair_visitor)(void* ctx, int64_t i, int64_t j);
 
 static int ssa_sequence(const ora_replica* rep, double r_cut, const double* q, int whole_box,
@@ -433,47 +444,44 @@ static int ssa_sequence(const ora_replica* rep, double r_cut, const double* q, i
         k[d] = whole_box ? cl.nc[d] : cl.k[d];
     }
     double dx[3];
-    for (int di = 0; di < 14; ++di) {
-        const int* del = ORA_DIRS[di];
-        int lead = del[2] != 0 ? 2 : (del[1] != 0 ? 1 : 0);
-        int odd_ring = (B[lead] == 1) && (k[lead] % 2 == 1);
-        int ncol = (di == 0) ? 1 : (odd_ring ? 3 : 2);
-        for (int col = 0; col < ncol; ++col) {
-            for (int cz = 0; cz < cl.nc[2]; ++cz)
-                for (int cy = 0; cy < cl.nc[1]; ++cy)
-                    for (int cx = 0; cx < cl.nc[0]; ++cx) {
-                        int cc[3] = {cx, cy, cz};
-                        int loc[3], brick[3], nb[3];
-                        for (int d = 0; d < 3; ++d) {
-                            loc[d] = cc[d] % k[d];
-                            brick[d] = cc[d] / k[d];
-                        }
-                        if (di > 0) {
-                            int l = loc[lead];
-                            int my_col = (odd_ring && l == k[lead] - 1) ? 2 : l % 2;
-                            if (my_col != col) continue;
-                        }
-                        int valid = 1;
-                        for (int d = 0; d < 3; ++d) {
-                            int ln = loc[d] + del[d];
-                            if (B[d] == 1) ln = (ln + k[d]) % k[d];
-                            else if (ln < 0 || ln >= k[d]) valid = 0;
-                            nb[d] = brick[d] * k[d] + ln;
-                        }
-                        if (!valid) continue;
-                        int64_t c0 = ((int64_t)cz * cl.nc[1] + cy) * cl.nc[0] + cx;
-                        int64_t c1 = ((int64_t)nb[2] * cl.nc[1] + nb[1]) * cl.nc[0] + nb[0];
-                        for (int64_t s = cl.start[c0]; s < cl.start[c0 + 1]; ++s) {
-                            int64_t i = cl.member[s];
-                            int64_t t0 = (di == 0) ? s + 1 : cl.start[c1];
-                            for (int64_t t = t0; t < cl.start[c1 + 1]; ++t) {
-                                int64_t j = cl.member[t];
-                                if (min_image(rep, q, i, j, dx) < r_cut * r_cut) visit(ctx, i, j);
+    for (int kz = 0; kz < 5; ++kz)
+        for (int ky = 0; ky < 5; ++ky)
+            for (int kx = 0; kx < 5; ++kx) {
+                int kcol[3] = {kx, ky, kz};
+                for (int cz = 0; cz < cl.nc[2]; ++cz)
+                    for (int cy = 0; cy < cl.nc[1]; ++cy)
+                        for (int cx = 0; cx < cl.nc[0]; ++cx) {
+                            int cc[3] = {cx, cy, cz}, loc[3], brick[3];
+                            int match = 1;
+                            for (int d = 0; d < 3; ++d) {
+                                loc[d] = cc[d] % k[d];
+                                brick[d] = cc[d] / k[d];
+                                if (axis_colour(loc[d], k[d], B[d] == 1) != kcol[d]) match = 0;
+                            }
+                            if (!match) continue;
+                            int64_t c0 = ((int64_t)cz * cl.nc[1] + cy) * cl.nc[0] + cx;
+                            for (int64_t si = cl.start[c0]; si < cl.start[c0 + 1]; ++si) {
+                                int64_t i = cl.member[si];
+                                for (int seg = 13; seg < 27; ++seg) {
+                                    int del[3] = {seg % 3 - 1, (seg / 3) % 3 - 1, seg / 9 - 1};
+                                    int nb[3], valid = 1;
+                                    for (int d = 0; d < 3; ++d) {
+                                        int ln = loc[d] + del[d];
+                                        if (B[d] == 1) ln = (ln + k[d]) % k[d];
+                                        else if (ln < 0 || ln >= k[d]) valid = 0;
+                                        nb[d] = brick[d] * k[d] + ln;
+                                    }
+                                    if (!valid) continue;
+                                    int64_t c1 = ((int64_t)nb[2] * cl.nc[1] + nb[1]) * cl.nc[0] + nb[0];
+                                    for (int64_t t = cl.start[c1]; t < cl.start[c1 + 1]; ++t) {
+                                        int64_t j = cl.member[t];
+                                        if (seg == 13 && j <= i) continue;
+                                        if (min_image(rep, q, i, j, dx) < r_cut * r_cut) visit(ctx, i, j);
+                                    }
+                                }
                             }
                         }
-                    }
-        }
-    }
+            }
     free_cells(&cl);
     return 0;
 }

@@ -168,6 +168,52 @@ def test_ssa_order_covers_each_pair_once(ora, bricks):
     assert len(got) == len(set(got)) and set(got) == intra
 
 
+@pytest.mark.parametrize("bricks,box", [((1, 1, 1), (6.934, 7.5, 9.7)), ((2, 2, 2), (6.934, 7.5, 9.7)),
+                                        ((1, 2, 3), (6.934, 7.5, 9.7)), ((3, 1, 1), (7.5, 4.2, 5.3)),
+                                        ((2, 1, 1), (4.1, 3.4, 5.3))])
+@pytest.mark.parametrize("whole_box", [False, True])
+def test_ssa_order_colour_classes_are_independent(ora, bricks, box, whole_box):
+    """The sequence is a run of colour classes; inside one class the pairs of
+    different cells touch disjoint particles, so any interleaving of those
+    cells (the parallel execution) applies the same maps to the same values.
+    Inside a cell, the first particles come in ascending id."""
+    n = int(3 * np.prod(box))
+    q, _, _ = state(n, box, seed=17)
+    rep = ora.make_replica(n, box, 100.0, bricks)
+    nc, k = ora.cell_grid(rep, 1.0)
+    cell = np.stack([np.minimum(nc[d] - 1, (q[:, d] * (nc[d] / box[d])).astype(int)) for d in range(3)], axis=1)
+    dom_k = np.array(nc if whole_box else k)
+    periodic = [whole_box or bricks[d] == 1 for d in range(3)]
+
+    def colour(c):
+        out = []
+        for d in range(3):
+            l = c[d] % dom_k[d]
+            full = 3 * (dom_k[d] // 3)
+            out.append(3 + l - full if periodic[d] and l >= full else l % 3)
+        return (out[2], out[1], out[0])
+
+    seq = ora.ssa_order(rep, 1.0, q, whole_box=whole_box)
+    assert len(seq) > 0
+    cols = [colour(cell[i]) for i, _ in seq]
+    assert cols == sorted(cols)                      # classes in lexicographic order
+    for col in set(cols):
+        idx = [u for u, c in enumerate(cols) if c == col]
+        touched = {}
+        for u in idx:
+            i, j = seq[u]
+            owner = tuple(cell[i])
+            for x in (i, j):
+                assert touched.setdefault(int(x), owner) == owner
+        # per cell, a contiguous block with i non-decreasing
+        owners = [tuple(cell[seq[u][0]]) for u in idx]
+        for o in set(owners):
+            pos = [v for v, w in enumerate(owners) if w == o]
+            assert pos == list(range(pos[0], pos[0] + len(pos)))
+            firsts = [seq[idx[v]][0] for v in pos]
+            assert firsts == sorted(firsts)
+
+
 # ---- statistics -----------------------------------------------------------------
 
 def test_ssa_map_matches_pair_sde(ora):
