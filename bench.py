@@ -221,7 +221,7 @@ def run_ours(args):
         "energy": {"rel_drift_over_timed_steps": drift, "steps": args.steps + args.warmup,
                    "status": status},
     }
-    nlaunch = count_launches(S, args.scheme)
+    nlaunch = S.step_launches(args.scheme)
     out["gpu_launches"] = nlaunch * args.steps
     if rank == 0:
         out["clocks"] = clk.summary()
@@ -231,16 +231,6 @@ def run_ours(args):
     S.close()
     if world > 1:
         tdist.destroy_process_group()
-
-
-def count_launches(S, scheme: str) -> int:
-    """Kernels of one step: kick-drift, 3 scan passes, scatter, gather, force,
-    step counter, plus the scheme's FD kernels (SSA: one launch per round)."""
-    base = 1 + 3 + 2 + 1 + 1
-    ssa_rounds = 0
-    if scheme in ("HYBRID", "SSA"):
-        ssa_rounds = 1 + 13 * 2   # at least; a third colour is added for odd periodic rings
-    return base + {"SER": 2, "HYBRID": ssa_rounds + 3, "SEM": 1, "SSA": ssa_rounds + 1}[scheme]
 
 
 def oracle_sample(w, n_target: int):

@@ -96,12 +96,15 @@
  *  The quotient ncell_d / L_d is formed once in double. A pair is "intra
  *  domain" (set A of Sec. III.B.2) iff both particles have the same brick.
  *  Order of the SSA sequence over A (the paper leaves it free, Sec. III.A.2):
- *   the cells are coloured per axis by their local coordinate l in the brick,
- *     col_d(l) = l mod 3, except that along an axis where the brick spans the
- *     replica (B_d = 1, periodic) the last k_d mod 3 cells take colours 3, 4;
+ *   the cells are coloured per axis by their local coordinate l in the brick
+ *   with period P_x = P_y = 3, P_z = 2 (the pairs of a cell reach offsets
+ *   -1..1 along x and y but only 0..1 along z):
+ *     col_d(l) = l mod P_d, except that along an axis where the brick spans
+ *     the replica (B_d = 1, periodic) the last k_d mod P_d cells take colours
+ *     P_d, P_d + 1;
  *   colours (col_z, col_y, col_x) are taken in lexicographic order (z major).
- *   Cells of one colour have disjoint 3x3x3 neighbourhoods inside their
- *   bricks and are processed in any order. Within a cell, its particles i in
+ *   The cells reached by the pairs of two cells of one colour are disjoint,
+ *   so those cells are processed in any order. Within a cell, its particles i in
  *   ascending id, each applying its forward pairs (i, j) in the order
  *   (segment, id_j): j lies in a neighbour cell of the same brick (wrapping
  *   only along B_d = 1 axes) at offset (dx, dy, dz) with segment

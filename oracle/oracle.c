@@ -411,22 +411,24 @@ static void ssa_pair(const fd_ctx* c, int64_t i, int64_t j)
     c->eps[j] -= 0.5 * dK;
 }
 
-/* Colour of a cell coordinate l along one axis of a domain with k cells:
- * l mod 3, except that along a periodic domain axis (one domain spanning the
- * replica) the trailing k mod 3 cells take colours 3 and 4, so that two
- * cells of equal colour are at least 3 cells apart around the ring. */
-static int axis_colour(int l, int k, int periodic)
+/* Colour of a cell coordinate l along one axis of a domain with k cells and
+ * colour period P (3 along x and y, 2 along z -- the forward half stencil
+ * spans offsets -1..1 along x and y but only 0..1 along z): l mod P, except
+ * that along a periodic domain axis (one domain spanning the replica) the
+ * trailing k mod P cells take colours P, P + 1, so that two cells of equal
+ * colour are at least P cells apart around the ring. */
+static int axis_colour(int l, int k, int P, int periodic)
 {
-    int full = 3 * (k / 3);
-    if (periodic && l >= full) return 3 + (l - full);
-    return l % 3;
+    int full = P * (k / P);
+    if (periodic && l >= full) return P + (l - full);
+    return l % P;
 }
 
 /* Enumerates the SSA sequence: visit(i, j) for each interacting pair of the
  * domain (Hybrid's set A: same brick; or the whole replica when whole_box),
  * in the order the library header defines: colours (cz, cy, cx) in
  * lexicographic order (z major); within a colour the cells are independent
- * (their 3x3x3 neighbourhoods are disjoint) and taken in any order; within a
+ * (the cells their pairs reach are disjoint) and taken in any order; within a
  * cell, particles i by ascending id, each applying its forward pairs -- the
  * partners j in the 27 neighbour cells of the same domain whose cell offset
  * segment 9 (dz+1) + 3 (dy+1) + (dx+1) exceeds 13, or equals 13 (same cell)
@@ -444,7 +446,8 @@ static int ssa_sequence(const ora_replica* rep, double r_cut, const double* q, i
         k[d] = whole_box ? cl.nc[d] : cl.k[d];
     }
     double dx[3];
-    for (int kz = 0; kz < 5; ++kz)
+    const int period[3] = {3, 3, 2};
+    for (int kz = 0; kz < 3; ++kz)
         for (int ky = 0; ky < 5; ++ky)
             for (int kx = 0; kx < 5; ++kx) {
                 int kcol[3] = {kx, ky, kz};
@@ -456,7 +459,7 @@ static int ssa_sequence(const ora_replica* rep, double r_cut, const double* q, i
                             for (int d = 0; d < 3; ++d) {
                                 loc[d] = cc[d] % k[d];
                                 brick[d] = cc[d] / k[d];
-                                if (axis_colour(loc[d], k[d], B[d] == 1) != kcol[d]) match = 0;
+                                if (axis_colour(loc[d], k[d], period[d], B[d] == 1) != kcol[d]) match = 0;
                             }
                             if (!match) continue;
                             int64_t c0 = ((int64_t)cz * cl.nc[1] + cy) * cl.nc[0] + cx;

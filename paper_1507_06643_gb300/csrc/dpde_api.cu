@@ -41,27 +41,19 @@ struct dpde_handle {
     int nchunks = 0;
     int nbr_cap = 0;
     bool mixed = false;
-    int need_col3_whole[14] = {0};
-    int need_col3_brick[14] = {0};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t cap_stream = nullptr;
     // device buffers
     void *qA = nullptr, *pA = nullptr, *qB = nullptr, *pB = nullptr, *F = nullptr, *dp = nullptr;
-    void *eA = nullptr, *eB = nullptr, *nbr_w = nullptr, *fwd_g = nullptr, *fwd_w = nullptr;
+    void *eA = nullptr, *eB = nullptr, *nbr_w = nullptr, *fwd_w = nullptr;
     int *cA = nullptr, *cB = nullptr, *nbr_j = nullptr, *nbr_n = nullptr, *fwd_j = nullptr, *fwd_n = nullptr;
-    int* fwd_cur = nullptr;
-    uint32_t* ssa_ent = nullptr;
-    void* ssa_gw = nullptr;
-    int* ssa_off = nullptr;
     int4 *tile_org = nullptr, *tile_dim = nullptr;
     int ntiles = 0;
-    int kc_max = 1;
-    int ssa_cap = 0;          // particles staged in shared memory per SSA block
-    int ssa_ccap = 0;         // cells per SSA block
-    int nssa_blocks = 0;
-    int4* ssa_blocks = nullptr;   // (replica, first brick, bricks, -)
-    size_t ssa_smem = 0;
+    // SSA colour classes: cells grouped by colour index (col_z * 5 + col_y) * 5
+    // + col_x, for the brick domains (Hybrid) and the whole replica (SSA)
+    int* col_cells[2] = {nullptr, nullptr};
+    std::vector<int> col_off[2];   // NCOLOURS + 1 offsets into col_cells
     int hcap = 0;             // halo particles staged per force tile
     size_t tile_smem = 0;
     uint32_t* idB = nullptr;
@@ -114,8 +106,7 @@ Ctx<T> make_ctx(dpde_handle* h) {
     C.key = h->key; C.tmp = h->tmp;
     C.count = h->cnt; C.fill = h->cnt + h->ncells; C.start = h->start;
     C.nbr_j = h->nbr_j; C.nbr_w = (T*)h->nbr_w; C.nbr_n = h->nbr_n; C.nbr_cap = h->nbr_cap;
-    C.fwd_j = h->fwd_j; C.fwd_g = (vec_t<T>*)h->fwd_g; C.fwd_w = (T*)h->fwd_w; C.fwd_n = h->fwd_n; C.fwd_cur = h->fwd_cur;
-    C.ssa_ent = h->ssa_ent; C.ssa_gw = (vec_t<T>*)h->ssa_gw; C.ssa_off = h->ssa_off;
+    C.fwd_j = h->fwd_j; C.fwd_w = (T*)h->fwd_w; C.fwd_n = h->fwd_n;
     C.rep_of_slot = h->rep_of_slot; C.rep_of_cell = h->rep_of_cell;
     C.brick_rep = h->brick_rep; C.tab = h->tab;
     C.reps = h->d_reps; C.step = h->d_step; C.status = h->d_status;
@@ -167,13 +158,15 @@ void enqueue_force(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T half_dt, 
     }
 }
 
+// The SSA sequence: one launch per non-empty colour class, in colour order.
 template <class T>
-void enqueue_ssa_rounds(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_dt, int whole) {
-    const int nbc = ceil_div(h->ncells, 256);
-    for (int di = 0; di < 14; ++di) {
-        const int three = whole ? h->need_col3_whole[di] : h->need_col3_brick[di];
-        const int ncol = di == 0 ? 1 : (three ? 3 : 2);
-        for (int col = 0; col < ncol; ++col) k_ssa_round<T><<<nbc, 256, 0, st>>>(C, di, col, whole, dt, sqrt_dt);
+void enqueue_ssa(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_dt, int whole) {
+    const std::vector<int>& off = h->col_off[whole];
+    for (int k = 0; k < NCOLOURS; ++k) {
+        const int n = off[k + 1] - off[k];
+        if (n > 0)
+            k_ssa_colour<T><<<ceil_div(n, SSA_THREADS), SSA_THREADS, 0, st>>>(C, h->col_cells[whole] + off[k], n,
+                                                                            dt, sqrt_dt);
     }
 }
 
@@ -189,13 +182,7 @@ void enqueue_step(dpde_handle* h, cudaStream_t st, double dt_d, int scheme) {
     phase(h, st, DPDE_PHASE_FORCE, 1);
     if (scheme == DPDE_HYBRID || scheme == DPDE_SSA) {
         phase(h, st, DPDE_PHASE_SSA, 0);
-        if (scheme == DPDE_SSA) {
-            k_fwd_gauss<T><<<nb, h->block, 0, st>>>(C);
-            enqueue_ssa_rounds<T>(h, C, st, dt, sqrt_dt, 1);
-        } else {
-            k_ssa_block<T><<<h->nssa_blocks, SSA_THREADS, h->ssa_smem, st>>>(C, h->ssa_blocks, dt, sqrt_dt,
-                                                                              h->ssa_cap, h->ssa_ccap);
-        }
+        enqueue_ssa<T>(h, C, st, dt, sqrt_dt, scheme == DPDE_SSA ? 1 : 0);
         phase(h, st, DPDE_PHASE_SSA, 1);
     }
     if (scheme == DPDE_SER || scheme == DPDE_HYBRID) {
@@ -259,7 +246,7 @@ void free_all(dpde_handle* h) {
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
     void* bufs[] = {h->qA, h->pA, h->qB, h->pB, h->F, h->dp, h->eA, h->eB, h->nbr_w, h->cA, h->cB, h->nbr_j,
-                    h->nbr_n, h->fwd_j, h->fwd_g, h->fwd_w, h->fwd_n, h->fwd_cur, h->tile_org, h->tile_dim, h->ssa_blocks, h->ssa_ent, h->ssa_gw, h->ssa_off, h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
+                    h->nbr_n, h->fwd_j, h->fwd_w, h->fwd_n, h->tile_org, h->tile_dim, h->col_cells[0], h->col_cells[1], h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
                     h->rep_of_cell, h->brick_rep, h->tab, h->chunk_rep, h->chunk_begin, h->chunk_end,
                     h->rep_chunk_begin, h->partial, h->obs_out, h->d_reps, h->d_step, h->d_status,
                     h->staging, h->cells_out};
@@ -292,7 +279,7 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     const int CHUNK = 4096;
     std::vector<int> chunk_rep, chunk_begin, chunk_end, rep_chunk_begin(1, 0), tabs, brick_rep;
     std::vector<int4> torg, tdim;
-    double rho_max = 0.0, per_cell_max = 0.0, per_brick_max = 0.0;
+    double rho_max = 0.0, per_cell_max = 0.0;
     for (int r = 0; r < n_replicas; ++r) {
         const dpde_replica& d = replicas[r];
         RepInfo I{};
@@ -337,8 +324,6 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         for (int a = 0; a < 3; ++a)
             for (int c = 0; c < I.nc[a]; ++c) tabs.push_back(c / I.k[a]);
         for (int b = 0; b < nbr; ++b) brick_rep.push_back(r);
-        h->kc_max = std::max(h->kc_max, kc);
-        per_brick_max = std::max(per_brick_max, (double)d.n / nbr);
         for (int z0 = 0; z0 < I.nc[2]; z0 += TILE_EDGE)
             for (int y0 = 0; y0 < I.nc[1]; y0 += TILE_EDGE)
                 for (int x0 = 0; x0 < I.nc[0]; x0 += TILE_EDGE) {
@@ -373,32 +358,6 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     h->nbr_cap = (int)std::ceil(3.0 * mean_nbr) + 32;
     const size_t vsz = h->mixed ? sizeof(float4) : sizeof(d4);
     const size_t esz = h->mixed ? sizeof(ff) : sizeof(double);
-    // SSA blocks: runs of consecutive bricks of one replica whose particles
-    // (1.1x the mean occupancy) fill the shared-memory budget
-    std::vector<int4> sblk;
-    {
-        const size_t tsz1 = h->mixed ? sizeof(float) : sizeof(double);
-        const size_t per = 3 * tsz1 + esz + 1;
-        const size_t budget = 200 * 1024;
-        int nbmax = 1;
-        for (int r = 0; r < h->R; ++r) {
-            const RepInfo& I = h->info[r];
-            const int kc = I.k[0] * I.k[1] * I.k[2];
-            const int nbr = I.B[0] * I.B[1] * I.B[2];
-            const double per_brick = 1.1 * (double)I.n / nbr + 16.0;
-            const double bytes_brick = per_brick * per + kc * sizeof(int);
-            int nb = (int)std::max(1.0, std::floor((double)(budget - 64) / bytes_brick));
-            nb = std::min(nb, nbr);
-            nbmax = std::max(nbmax, nb);
-            for (int b0 = 0; b0 < nbr; b0 += nb) sblk.push_back(make_int4(r, I.brick_off + b0, std::min(nb, nbr - b0), 0));
-        }
-        h->nssa_blocks = (int)sblk.size();
-        h->ssa_ccap = nbmax * h->kc_max;
-        const size_t head = ((size_t)(h->ssa_ccap + 1) * sizeof(int) + 15) & ~(size_t)15;
-        h->ssa_cap = (int)std::max<double>(0.0, std::min<double>(255.0 * 1024 * 1024,
-                                                                 (double)((budget - head - 16) / per)));
-        h->ssa_smem = 16 + head + (size_t)h->ssa_cap * per + 16;
-    }
     // force tiles: halo of (TILE_EDGE + 2)^3 cells staged up to 1.15x the mean + 64
     {
         const size_t vsz0 = vsz;
@@ -412,16 +371,39 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
                                         (double)((smem_limit - thead) / tper));
         h->tile_smem = 32 + thead + (size_t)h->hcap * tper;
     }
-    // colours per SSA direction for the whole-replica SSA: three when the
-    // leading axis has an odd number of cells
-    static const int dirs[14][3] = {{0, 0, 0},   {1, 0, 0},  {-1, 1, 0}, {0, 1, 0},  {1, 1, 0},
-                                    {-1, -1, 1}, {0, -1, 1}, {1, -1, 1}, {-1, 0, 1}, {0, 0, 1},
-                                    {1, 0, 1},   {-1, 1, 1}, {0, 1, 1},  {1, 1, 1}};
-    for (int di = 1; di < 14; ++di) {
-        const int lead = dirs[di][2] ? 2 : (dirs[di][1] ? 1 : 0);
+    // SSA colour classes (cell colours of the SSA order, per axis l mod P
+    // with P = 3, 3, 2 along x, y, z, and colours P, P + 1 for the last
+    // k mod P cells of a periodic domain axis), for brick domains (m = 0)
+    // and whole replicas (m = 1)
+    std::vector<int> col_cells[2];
+    for (int m = 0; m < 2; ++m) {
+        std::vector<std::vector<int>> cls(NCOLOURS);
         for (const RepInfo& I : h->info) {
-            if (I.nc[lead] & 1) h->need_col3_whole[di] = 1;
-            if (I.B[lead] == 1 && (I.k[lead] & 1)) h->need_col3_brick[di] = 1;
+            const int* tx = tabs.data() + I.tab_off;
+            const int* ty = tx + I.nc[0];
+            const int* tz = ty + I.nc[1];
+            int col[3][1024];
+            for (int a = 0; a < 3; ++a) {
+                const bool periodic = m == 1 || I.B[a] == 1;
+                const int k = m == 1 ? I.nc[a] : I.k[a];
+                const int P = a == 2 ? 2 : 3;
+                const int full = P * (k / P);
+                for (int c = 0; c < I.nc[a]; ++c) {
+                    const int l = m == 1 ? c : c % I.k[a];
+                    col[a][c] = (periodic && l >= full) ? P + (l - full) : l % P;
+                }
+            }
+            for (int z = 0; z < I.nc[2]; ++z)
+                for (int y = 0; y < I.nc[1]; ++y)
+                    for (int x = 0; x < I.nc[0]; ++x)
+                        cls[(col[2][z] * 5 + col[1][y]) * 5 + col[0][x]].push_back(I.cell_off + tx[x] + ty[y] +
+                                                                                   tz[z]);
+        }
+        h->col_off[m].assign(1, 0);
+        for (auto& v : cls) {
+            std::sort(v.begin(), v.end());
+            col_cells[m].insert(col_cells[m].end(), v.begin(), v.end());
+            h->col_off[m].push_back((int)col_cells[m].size());
         }
     }
     auto bail = [&](cudaError_t e, const char* what) {
@@ -460,10 +442,8 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     CKC(cudaMalloc(&h->nbr_w, tsz * n1 * (size_t)h->nbr_cap));
     CKC(cudaMalloc(&h->nbr_n, sizeof(int) * n1));
     CKC(cudaMalloc(&h->fwd_j, sizeof(int) * n1 * (size_t)h->nbr_cap));
-    CKC(cudaMalloc(&h->fwd_g, vsz * n1 * (size_t)h->nbr_cap));
     CKC(cudaMalloc(&h->fwd_w, tsz * n1 * (size_t)h->nbr_cap));
     CKC(cudaMalloc(&h->fwd_n, sizeof(int) * n1));
-    CKC(cudaMalloc(&h->fwd_cur, sizeof(int) * n1));
     CKC(cudaMalloc(&h->tile_org, sizeof(int4) * torg.size()));
     CKC(cudaMalloc(&h->tile_dim, sizeof(int4) * tdim.size()));
     CKC(cudaMalloc(&h->key, sizeof(int) * n1));
@@ -516,17 +496,13 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         CKC(cudaMemset(h->F, 0, vsz * n1));
         CKC(cudaMemset(h->nbr_n, 0, sizeof(int) * n1));
         CKC(cudaMemset(h->fwd_n, 0, sizeof(int) * n1));
-        CKC(cudaMemset(h->fwd_cur, 0, sizeof(int) * n1));
     }
-    CKC(cudaMalloc(&h->ssa_blocks, sizeof(int4) * sblk.size()));
-    CKC(cudaMalloc(&h->ssa_ent, sizeof(uint32_t) * n1 * SSA_ENT_PER_SLOT));
-    CKC(cudaMalloc(&h->ssa_gw, vsz * n1 * SSA_ENT_PER_SLOT));
-    CKC(cudaMalloc(&h->ssa_off, sizeof(int) * 14 * (c1 + sblk.size())));
-    CKC(cudaMemcpy(h->ssa_blocks, sblk.data(), sizeof(int4) * sblk.size(), cudaMemcpyHostToDevice));
-    if (h->mixed)
-        CKC(cudaFuncSetAttribute(k_ssa_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ssa_smem));
-    else
-        CKC(cudaFuncSetAttribute(k_ssa_block<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->ssa_smem));
+    for (int m = 0; m < 2; ++m) {
+        CKC(cudaMalloc(&h->col_cells[m], sizeof(int) * c1));
+        if (!col_cells[m].empty())
+            CKC(cudaMemcpy(h->col_cells[m], col_cells[m].data(), sizeof(int) * col_cells[m].size(),
+                           cudaMemcpyHostToDevice));
+    }
     {
         const int sm = (int)h->tile_smem;
         if (h->mixed) {
@@ -637,6 +613,23 @@ int dpde_step(dpde_handle* h, int64_t n, double dt, int32_t scheme, int32_t use_
         CK(h, cudaGetLastError());
     }
     h->step += n;
+    return DPDE_OK;
+}
+
+int dpde_step_launches(dpde_handle* h, int32_t scheme, int64_t* launches) {
+    if (!h || !launches) return DPDE_ERR_ARG;
+    if (scheme < DPDE_SER || scheme > DPDE_SSA) return fail(h, DPDE_ERR_ARG, "bad scheme");
+    *launches = 0;
+    if (h->N == 0) return DPDE_OK;
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_step_any(h, h->cap_stream, 0.01, scheme);
+    CK(h, cudaStreamEndCapture(h->cap_stream, &g));
+    size_t nodes = 0;
+    const cudaError_t e = cudaGraphGetNodes(g, nullptr, &nodes);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphGetNodes");
+    *launches = (int64_t)nodes;
     return DPDE_OK;
 }
 

@@ -29,15 +29,10 @@ template <class T> struct Ctx {
     T* nbr_w;        // 1 - r/r_cut of each entry
     int* nbr_n;      // entries per particle
     int nbr_cap;
-    int* fwd_j;      // forward pairs of the SSA, [k * N + i],
-                     //   packed t | direction << 27, in (direction, t) order
+    int* fwd_j;      // forward pairs of the SSA, particle-major rows [i * nbr_cap + k],
+                     //   partner slots in SSA sequence order (segment, id)
     T* fwd_w;        //   w = 1 - r/r_cut of each entry
-    vec* fwd_g;      //   G_it of each entry (x, y, z)
     int* fwd_n;
-    int* fwd_cur;    // SSA cursor into each forward list
-    uint32_t* ssa_ent;   // Hybrid SSA buckets: s | t << 16 (block-local slots),
-    vec* ssa_gw;         //   (G, w), per block region [first slot * SSA_ENT_PER_SLOT ...)
-    int* ssa_off;        //   chain offsets, 14 per cell (+14 per block)
     const int* rep_of_slot;
     const int* rep_of_cell;
     const int* brick_rep;
@@ -377,12 +372,11 @@ __global__ void k_copy_back(Ctx<T> C) {
 //              and forward neighbours in the same brick         -> fwd
 //   LIST_FWD   forward neighbours (whole-replica SSA)           -> fwd
 // A forward neighbour of i lies in the half stencil (segment > 13) or in
-// i's own cell after i; its segment - 13 is the SSA direction index, and the
-// visiting order (segment, slot) is the SSA sequence order of i's pairs.
-// Segment s = 9 (dz+1) + 3 (dy+1) + (dx+1) for the neighbour cell offset.
+// i's own cell after i. Both force paths visit the neighbour cells in
+// increasing segment s = 9 (dz+1) + 3 (dy+1) + (dx+1) and each cell in slot
+// (= id) order, so a forward row lists i's pairs in SSA sequence order.
 // ---------------------------------------------------------------------------
-constexpr int NBR_J_BITS = 27;   // slot bits of a packed forward entry
-constexpr int NBR_J_MASK = (1 << NBR_J_BITS) - 1;
+constexpr int NBR_J_BITS = 27;   // particle count limit 2^27 of a handle
 
 template <class T> __device__ __forceinline__ T trsqrt(T x);
 template <> __device__ __forceinline__ float trsqrt(float x) { return rsqrtf(x); }
@@ -418,8 +412,8 @@ __device__ __forceinline__ void force_hit(const Ctx<T>& C, int i, int j, uint32_
         ++o.nn;
     } else if ((LM == LIST_CROSS || LM == LIST_FWD) && (seg > 13 || (seg == 13 && j > i))) {
         if (o.nf < C.nbr_cap) {
-            const size_t at = (size_t)o.nf * N + i;
-            C.fwd_j[at] = j | ((seg - 13) << NBR_J_BITS);
+            const size_t at = (size_t)i * C.nbr_cap + o.nf;
+            C.fwd_j[at] = j;
             C.fwd_w[at] = w;
         }
         ++o.nf;
@@ -434,10 +428,7 @@ __device__ __forceinline__ void force_finish(const Ctx<T>& C, int i, T half_dt, 
         o.nf = min(o.nf, C.nbr_cap);
     }
     if (LM == LIST_ALL || LM == LIST_CROSS) C.nbr_n[i] = o.nn;
-    if (LM == LIST_CROSS || LM == LIST_FWD) {
-        C.fwd_n[i] = o.nf;
-        C.fwd_cur[i] = 0;
-    }
+    if (LM == LIST_CROSS || LM == LIST_FWD) C.fwd_n[i] = o.nf;
     vec_t<T> f;
     f.x = o.fx; f.y = o.fy; f.z = o.fz; f.w = T(0);
     C.F[i] = f;
@@ -777,310 +768,196 @@ __global__ void k_sem(Ctx<T> C, T dt, T sqrt_dt) {
 }
 
 // ---------------------------------------------------------------------------
-// SSA pair map, Eq. (SSA_ij), on the pair (s, t) of the given arrays (shared
-// or global memory): exact OU transition of p_st at fixed gamma_st, then
-// eps_s, eps_t each absorb -Delta K_st / 2.
+// SSA (Sec. III.A.2 and III.B.2): the pair map of Eq. (SSA_ij) -- the exact
+// OU transition of p_st at fixed gamma_st, after which eps_s and eps_t each
+// absorb -Delta K_st / 2 -- applied pair after pair in sequence order.
+// One launch per cell colour class; one thread per cell of the class. The
+// cells reached by the pairs of two cells of one class are disjoint, so the
+// threads touch disjoint particles and update set B in place.
+// A thread walks its cell's chain -- the forward rows of the cell's
+// particles s in slot (= id) order, concatenated -- as one flat loop, so the
+// lanes of a warp diverge only by chain length. (p_s, eps_s, beta_s) stay in
+// registers while s is current; the partner's updated (p_t, eps_t) goes back
+// to memory at once, with beta_t = C_v / eps_t in p_t.w, so p.w is the
+// current beta of every particle throughout.
+// The loop is software-pipelined so that only the pair map itself is on the
+// critical path: partner indices are loaded two entries ahead, the partner
+// state (and the next particle's state on a row change) and the Gaussian
+// one entry ahead. Loads issued ahead of a store can alias it only for the
+// partner t being updated (two rows of a cell may share a partner, and a
+// later particle of the cell may itself be t); those take the new values
+// from registers.
 // ---------------------------------------------------------------------------
-__constant__ int c_dirs[14][3] = {{0, 0, 0},   {1, 0, 0},  {-1, 1, 0}, {0, 1, 0},  {1, 1, 0},
-                                  {-1, -1, 1}, {0, -1, 1}, {1, -1, 1}, {-1, 0, 1}, {0, 0, 1},
-                                  {1, 0, 1},   {-1, 1, 1}, {0, 1, 1},  {1, 1, 1}};
+constexpr int SSA_THREADS = 64;
+constexpr int SSA_ROWS = 20;     // rows per cell held in the shared row table
+constexpr int NCOLOURS = 75;     // (2 + 1) x (3 + 2) x (3 + 2) cell colours
 
-// The state-dependent part of the SSA pair map, with w = 1 - r/r_cut and the
-// Gaussian G_st already known.
+// The pair map on (p_s, eps_s, beta_s) in registers and partner (p_t, eps_t)
+// with beta_t = p_t.w; returns the new partner state, beta in .w.
 template <class T>
-__device__ __forceinline__ void ssa_apply(const Ctx<T>& C, const RepInfo& R, vec_t<T>* p, eps_t<T>* e,
-                                          int s, int t, T w, T3<T> G, T dt, T sqrt_dt) {
-    const vec_t<T> ps = p[s], pt = p[t];
-    const eps_t<T> es = e[s], et = e[t];
+__device__ __forceinline__ void ssa_pair_map(const Ctx<T>& C, const RepInfo& R, vec_t<T>& ps, eps_t<T>& es,
+                                             T& bs, vec_t<T>& pt, eps_t<T>& et, T w, const T3<T>& G, T dt,
+                                             T amp0) {
     const T chi = w * w;
-    const T gam = C.sig2_4 * (beta_of(es, R) + beta_of(et, R));
-    const T a = T(2) * gam * chi * dt * C.inv_m;
-    const T amp = (gam != T(0)) ? C.sigma * tsqrt(C.m * (-texpm1(T(-2) * a)) / gam)
-                                : T(2) * C.sigma * w * sqrt_dt;
-    const T em1 = texpm1(-a);
+    const T gam = C.sig2_4 * (bs + pt.w);
+    const T aa = T(2) * gam * chi * dt * C.inv_m;
+    const T amp = (gam != T(0)) ? C.sigma * tsqrt(C.m * (-texpm1(T(-2) * aa)) / gam) : amp0 * w;
+    const T em1 = texpm1(-aa);
     const T Dx = T(0.5) * (em1 * (ps.x - pt.x) + amp * G.x);
     const T Dy = T(0.5) * (em1 * (ps.y - pt.y) + amp * G.y);
     const T Dz = T(0.5) * (em1 * (ps.z - pt.z) + amp * G.z);
-    vec_t<T> sn = ps, tn = pt;
-    sn.x = ps.x + Dx; sn.y = ps.y + Dy; sn.z = ps.z + Dz;
-    tn.x = pt.x - Dx; tn.y = pt.y - Dy; tn.z = pt.z - Dz;
+    const T snx = ps.x + Dx, sny = ps.y + Dy, snz = ps.z + Dz;
+    const T tnx = pt.x - Dx, tny = pt.y - Dy, tnz = pt.z - Dz;
     // kinetic-energy change of the stored momenta, halved
-    const T dK = ((sn.x - ps.x) * (sn.x + ps.x) + (sn.y - ps.y) * (sn.y + ps.y) +
-                  (sn.z - ps.z) * (sn.z + ps.z) + (tn.x - pt.x) * (tn.x + pt.x) +
-                  (tn.y - pt.y) * (tn.y + pt.y) + (tn.z - pt.z) * (tn.z + pt.z)) *
+    const T dK = ((snx - ps.x) * (snx + ps.x) + (sny - ps.y) * (sny + ps.y) + (snz - ps.z) * (snz + ps.z) +
+                  (tnx - pt.x) * (tnx + pt.x) + (tny - pt.y) * (tny + pt.y) + (tnz - pt.z) * (tnz + pt.z)) *
                  (T(0.25) * C.inv_m);
-    p[s] = sn;
-    p[t] = tn;
-    e[s] = eps_add(es, -dK);
-    e[t] = eps_add(et, -dK);
+    ps.x = snx; ps.y = sny; ps.z = snz;
+    es = eps_add(es, -dK);
+    bs = beta_of(es, R);
+    pt.x = tnx; pt.y = tny; pt.z = tnz;
+    et = eps_add(et, -dK);
+    pt.w = beta_of(et, R);
 }
 
-// One round (direction di, colour col) of the SSA sequence, as one launch
-// over every cell of every replica. The pairs of cell pair (c, c + delta_di)
-// are the direction-di entries of the forward lists of c's particles, in
-// sequence order; a per-particle cursor walks each forward list across the
-// rounds. Cell pairs of a round touch disjoint particles, so the pair maps
-// update set B in place. whole_box: the domain is the whole replica (the
-// DPDE_SSA scheme) rather than the brick (Hybrid's set A).
+// Plain (unpipelined) chain, for cells with more than SSA_ROWS rows.
 template <class T>
-__global__ void k_ssa_round(Ctx<T> C, int di, int col, int whole_box, T dt, T sqrt_dt) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C.ncells) return;
-    const int b = C.start[c], e = C.start[c + 1];
-    if (b == e) return;
-    const int rep = C.rep_of_cell[c];
-    const RepInfo& R = C.reps[rep];
-    if (di > 0) {
-        // colour: coordinate of c along the leading axis, inside its domain
-        const int kx = R.k[0], ky = R.k[1], kz = R.k[2];
-        const int kc = kx * ky * kz;
-        const int rel = c - R.cell_off;
-        const int bi = rel / kc, li = rel - bi * kc;
-        const int dyo = c_dirs[di][1], dzo = c_dirs[di][2];
-        const int lead = dzo != 0 ? 2 : (dyo != 0 ? 1 : 0);
-        int l, kl, Bl;
-        if (lead == 0) {
-            l = li % kx; kl = kx; Bl = R.B[0];
-            if (whole_box) l += (bi % R.B[0]) * kx;
-        } else if (lead == 1) {
-            l = (li / kx) % ky; kl = ky; Bl = R.B[1];
-            if (whole_box) l += ((bi / R.B[0]) % R.B[1]) * ky;
-        } else {
-            l = li / (kx * ky); kl = kz; Bl = R.B[2];
-            if (whole_box) l += (bi / (R.B[0] * R.B[1])) * kz;
-        }
-        if (whole_box) { kl = R.nc[lead]; Bl = 1; }
-        const bool odd = (Bl == 1) && (kl & 1);
-        const int my = (odd && l == kl - 1) ? 2 : (l & 1);
-        if (my != col) return;
-    }
+__device__ void ssa_chain_plain(const Ctx<T>& C, const RepInfo& R, int rep, int b, int e, uint32_t step, T dt,
+                                T amp0) {
+    const size_t cap = (size_t)C.nbr_cap;
     for (int s = b; s < e; ++s) {
         const int nf = C.fwd_n[s];
-        int m = C.fwd_cur[s];
-        for (; m < nf; ++m) {
-            const size_t at = (size_t)m * C.N + s;
-            const int packed = C.fwd_j[at];
-            if ((packed >> NBR_J_BITS) != di) break;
-            const vec_t<T> g = C.fwd_g[at];
-            ssa_apply(C, R, C.pB, C.eB, s, packed & NBR_J_MASK, C.fwd_w[at], T3<T>{g.x, g.y, g.z}, dt, sqrt_dt);
-        }
-        C.fwd_cur[s] = m;
-    }
-}
-
-// Hybrid's SSA over set A. A block owns a run of consecutive domains
-// ("bricks") of one replica -- a contiguous slot range in brick-major cell
-// order -- so that every round has thousands of independent cell pairs
-// between two barriers. Momenta (x, y, z arrays) and internal energies are
-// staged in shared memory when they fit (else the block works on global
-// memory in place).
-// Prologue: each thread owns a contiguous run of cells; it counts its
-// particles' forward entries per direction, 14 block scans place them, and
-// the thread writes every entry (s, t, G, w) into its direction's bucket in
-// sequence order -- drawing the Gaussians with all lanes busy -- together
-// with each cell's chain offsets. Rounds (direction di, colour col): each
-// thread takes cell pairs (c, c + delta_di) of colour col and applies the
-// chain of c from the di bucket, in order. Writes set B back with beta
-// refreshed. Blocks whose entries exceed their bucket region run the chains
-// directly from the forward lists with inline Gaussians.
-constexpr int SSA_THREADS = 1024;
-constexpr int SSA_ENT_PER_SLOT = 12;   // bucket capacity per particle (mean ~5.4 at density 3)
-
-template <class T>
-__device__ __forceinline__ void ssa_map_smem(const Ctx<T>& C, const RepInfo& R, T* px, T* py, T* pz,
-                                             eps_t<T>* se, int s, int t, const vec_t<T>& gw, T dt,
-                                             T sqrt_dt) {
-    // the pair map of Eq. (SSA_ij) at fixed gamma_st (as in ssa_apply)
-    const T psx = px[s], psy = py[s], psz = pz[s];
-    const T ptx = px[t], pty = py[t], ptz = pz[t];
-    const eps_t<T> es = se[s], et = se[t];
-    const T w = gw.w;
-    const T chi = w * w;
-    const T gam = C.sig2_4 * (beta_of(es, R) + beta_of(et, R));
-    const T aa = T(2) * gam * chi * dt * C.inv_m;
-    const T amp = (gam != T(0)) ? C.sigma * tsqrt(C.m * (-texpm1(T(-2) * aa)) / gam)
-                                : T(2) * C.sigma * w * sqrt_dt;
-    const T em1 = texpm1(-aa);
-    const T Dx = T(0.5) * (em1 * (psx - ptx) + amp * gw.x);
-    const T Dy = T(0.5) * (em1 * (psy - pty) + amp * gw.y);
-    const T Dz = T(0.5) * (em1 * (psz - ptz) + amp * gw.z);
-    const T snx = psx + Dx, sny = psy + Dy, snz = psz + Dz;
-    const T tnx = ptx - Dx, tny = pty - Dy, tnz = ptz - Dz;
-    const T dK = ((snx - psx) * (snx + psx) + (sny - psy) * (sny + psy) + (snz - psz) * (snz + psz) +
-                  (tnx - ptx) * (tnx + ptx) + (tny - pty) * (tny + pty) + (tnz - ptz) * (tnz + ptz)) *
-                 (T(0.25) * C.inv_m);
-    px[s] = snx; py[s] = sny; pz[s] = snz;
-    px[t] = tnx; py[t] = tny; pz[t] = tnz;
-    se[s] = eps_add(es, -dK);
-    se[t] = eps_add(et, -dK);
-}
-
-template <class T>
-__global__ void __launch_bounds__(SSA_THREADS) k_ssa_block(Ctx<T> C, const int4* __restrict__ blocks, T dt,
-                                                           T sqrt_dt, int pcap, int ccap) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    using vec = vec_t<T>;
-    using E = eps_t<T>;
-    const int4 blk = blocks[blockIdx.x];   // (replica, first brick, number of bricks, -)
-    const int rep = blk.x;
-    const RepInfo& R = C.reps[rep];
-    const int kx = R.k[0], ky = R.k[1], kz = R.k[2];
-    const int kc = kx * ky * kz;
-    const int ncell = blk.z * kc;
-    const int first = R.cell_off + (blk.y - R.brick_off) * kc;
-    const int base = C.start[first];
-    const int cnt = C.start[first + ncell] - base;
-    const size_t N = (size_t)C.N;
-    // shared layout: sst[ccap+1] | px py pz [pcap] | e[pcap] ; small arrays below
-    unsigned char* sm = (unsigned char*)(((size_t)smem_raw + 15) & ~(size_t)15);
-    int* sst = (int*)sm;
-    T* px = (T*)(sm + (((size_t)(ccap + 1) * sizeof(int) + 15) & ~(size_t)15));
-    T* py = px + pcap;
-    T* pz = py + pcap;
-    E* se = (E*)((((size_t)(pz + pcap)) + 7) & ~(size_t)7);
-    __shared__ int bbase[15];
-    __shared__ int scan_sh[32];
-    const bool in_smem = cnt <= pcap;
-    for (int c = threadIdx.x; c <= ncell; c += blockDim.x) sst[c] = C.start[first + c] - base;
-    if (in_smem)
-        for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
-            const vec pv = C.pB[base + s];
-            px[s] = pv.x; py[s] = pv.y; pz[s] = pv.z;
-            se[s] = C.eB[base + s];
-        }
-    __syncthreads();
-    // --- prologue: bucket the forward entries by direction ---
-    const int cpt = (ncell + SSA_THREADS - 1) / SSA_THREADS;
-    const int c0 = min(ncell, (int)threadIdx.x * cpt), c1 = min(ncell, c0 + cpt);
-    int run[14];
-#pragma unroll
-    for (int d = 0; d < 14; ++d) run[d] = 0;
-    for (int s = sst[c0]; s < sst[c1]; ++s) {
-        const int nf = C.fwd_n[base + s];
+        if (nf == 0) continue;
+        vec_t<T> ps = C.pB[s];
+        eps_t<T> es = C.eB[s];
+        T bs = ps.w;
+        const uint32_t ids = C.idB[s];
         for (int m = 0; m < nf; ++m) {
-            const int d = C.fwd_j[(size_t)m * N + base + s] >> NBR_J_BITS;
-#pragma unroll
-            for (int dd = 0; dd < 14; ++dd) run[dd] += (dd == d) ? 1 : 0;
+            const int t = C.fwd_j[(size_t)s * cap + m];
+            const T w = C.fwd_w[(size_t)s * cap + m];
+            vec_t<T> pt = C.pB[t];
+            eps_t<T> et = C.eB[t];
+            const T3<T> G = pair_gauss<T>(C.seed, step, (uint32_t)rep, ids, C.idB[t]);
+            ssa_pair_map(C, R, ps, es, bs, pt, et, w, G, dt, amp0);
+            C.pB[t] = pt;
+            C.eB[t] = et;
         }
-    }
-    int total = 0;
-#pragma unroll
-    for (int d = 0; d < 14; ++d) {
-        int tot;
-        const int ex = block_exclusive_scan(run[d], scan_sh, tot);
-        run[d] = ex;
-        if (threadIdx.x == 0) bbase[d] = total;
-        total += tot;
-    }
-    if (threadIdx.x == 0) bbase[14] = total;
-    const size_t ebase = (size_t)base * SSA_ENT_PER_SLOT;   // this block's bucket region
-    const bool bucketed = in_smem && total <= cnt * SSA_ENT_PER_SLOT;   // uniform
-    int* off = C.ssa_off + (size_t)(first + blockIdx.x) * 14;
-    __syncthreads();
-    if (bucketed) {
-        const uint32_t step = (uint32_t)*C.step;
-        for (int c = c0; c < c1; ++c) {
-#pragma unroll
-            for (int d = 0; d < 14; ++d) off[(size_t)c * 14 + d] = bbase[d] + run[d];
-            for (int s = sst[c]; s < sst[c + 1]; ++s) {
-                const int nf = C.fwd_n[base + s];
-                const uint32_t ids = C.idB[base + s];
-                for (int m = 0; m < nf; ++m) {
-                    const size_t at = (size_t)m * N + base + s;
-                    const int packed = C.fwd_j[at];
-                    const int d = packed >> NBR_J_BITS;
-                    const int t = (packed & NBR_J_MASK) - base;
-                    int pos = 0;
-#pragma unroll
-                    for (int dd = 0; dd < 14; ++dd)
-                        if (dd == d) pos = bbase[dd] + run[dd]++;
-                    const T3<T> G = pair_gauss<T>(C.seed, step, (uint32_t)rep, ids, C.idB[base + t]);
-                    vec gw;
-                    gw.x = G.x; gw.y = G.y; gw.z = G.z; gw.w = C.fwd_w[at];
-                    C.ssa_ent[ebase + pos] = (uint32_t)s | ((uint32_t)t << 16);
-                    C.ssa_gw[ebase + pos] = gw;
-                }
-            }
-        }
-        if (threadIdx.x == 0)
-            for (int d = 0; d < 14; ++d) off[(size_t)ncell * 14 + d] = bbase[d + 1];
-    }
-    __syncthreads();
-    // --- rounds ---
-    const int Bx = R.B[0], By = R.B[1], Bz = R.B[2];
-    const uint32_t step = (uint32_t)*C.step;
-    for (int di = 0; di < 14; ++di) {
-        const int dyo = c_dirs[di][1], dzo = c_dirs[di][2];
-        const int lead = dzo != 0 ? 2 : (dyo != 0 ? 1 : 0);
-        const int klead = lead == 2 ? kz : (lead == 1 ? ky : kx);
-        const int Blead = lead == 2 ? Bz : (lead == 1 ? By : Bx);
-        const bool odd = (Blead == 1) && (klead & 1);
-        const int ncol = di == 0 ? 1 : (odd ? 3 : 2);
-        for (int col = 0; col < ncol; ++col) {
-            for (int cg = threadIdx.x; cg < ncell; cg += blockDim.x) {
-                if (di > 0) {
-                    const int c = cg % kc;
-                    const int lxc = c % kx, lyc = (c / kx) % ky, lzc = c / (kx * ky);
-                    const int ll = lead == 2 ? lzc : (lead == 1 ? lyc : lxc);
-                    const int my = (odd && ll == klead - 1) ? 2 : (ll & 1);
-                    if (my != col) continue;
-                }
-                if (bucketed) {
-                    const int m1 = off[(size_t)(cg + 1) * 14 + di];
-                    for (int m = off[(size_t)cg * 14 + di]; m < m1; ++m) {
-                        const uint32_t ent = C.ssa_ent[ebase + m];
-                        ssa_map_smem(C, R, px, py, pz, se, (int)(ent & 0xffffu), (int)(ent >> 16),
-                                     C.ssa_gw[ebase + m], dt, sqrt_dt);
-                    }
-                } else {
-                    // direct chains from the forward lists (global memory), inline Gaussians
-                    for (int s = C.start[first + cg] - base; s < C.start[first + cg + 1] - base; ++s) {
-                        const int nf = C.fwd_n[base + s];
-                        int m = C.fwd_cur[base + s];
-                        for (; m < nf; ++m) {
-                            const size_t at = (size_t)m * N + base + s;
-                            const int packed = C.fwd_j[at];
-                            if ((packed >> NBR_J_BITS) != di) break;
-                            const int t = packed & NBR_J_MASK;
-                            ssa_apply(C, R, C.pB, C.eB, base + s, t, C.fwd_w[at],
-                                      pair_gauss<T>(C.seed, step, (uint32_t)rep, C.idB[base + s], C.idB[t]), dt,
-                                      sqrt_dt);
-                        }
-                        C.fwd_cur[base + s] = m;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    for (int s = threadIdx.x; s < cnt; s += blockDim.x) {
-        vec pv = C.pB[base + s];
-        if (bucketed) {
-            pv.x = px[s]; pv.y = py[s]; pv.z = pz[s];
-            C.eB[base + s] = se[s];
-        }
-        pv.w = beta_of(C.eB[base + s], R);
-        C.pB[base + s] = pv;
+        ps.w = bs;
+        C.pB[s] = ps;
+        C.eB[s] = es;
     }
 }
 
-// Gaussians for the whole-replica SSA scheme (its rounds are separate launches).
 template <class T>
-__global__ void k_fwd_gauss(Ctx<T> C) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= C.N) return;
-    const int nf = C.fwd_n[s];
-    const uint32_t ids = C.idB[s];
-    const uint32_t rep = (uint32_t)C.rep_of_slot[s];
-    const uint32_t step = (uint32_t)*C.step;
-    for (int m = 0; m < nf; ++m) {
-        const size_t at = (size_t)m * C.N + s;
-        const int t = C.fwd_j[at] & NBR_J_MASK;
-        const T3<T> G = pair_gauss<T>(C.seed, step, rep, ids, C.idB[t]);
-        vec_t<T> g;
-        g.x = G.x; g.y = G.y; g.z = G.z; g.w = T(0);
-        C.fwd_g[at] = g;
+__global__ void __launch_bounds__(SSA_THREADS) k_ssa_colour(Ctx<T> C, const int* __restrict__ cells, int ncol,
+                                                            T dt, T sqrt_dt) {
+    __shared__ int row_s[SSA_ROWS][SSA_THREADS];   // slot of each non-empty row
+    __shared__ int row_n[SSA_ROWS][SSA_THREADS];   // its entry count
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= ncol) return;
+    const int tid = threadIdx.x;
+    const int c = cells[u];
+    const int b = C.start[c], e = C.start[c + 1];
+    int nrow = 0, total = 0;
+    for (int s = b; s < e; ++s) {
+        const int nf = C.fwd_n[s];
+        if (nf > 0) {
+            if (nrow < SSA_ROWS) {
+                row_s[nrow][tid] = s;
+                row_n[nrow][tid] = nf;
+            }
+            ++nrow;
+            total += nf;
+        }
     }
+    if (total == 0) return;
+    const int rep = C.rep_of_cell[c];
+    const RepInfo& R = C.reps[rep];
+    const uint32_t step = (uint32_t)*C.step;
+    const T amp0 = T(2) * C.sigma * sqrt_dt;   // amplitude of the map as gamma -> 0
+    if (nrow > SSA_ROWS) {
+        ssa_chain_plain(C, R, rep, b, e, step, dt, amp0);
+        return;
+    }
+    const size_t cap = (size_t)C.nbr_cap;
+    // position (r, m) of an entry; advancing past the last entry stays there
+    auto advance = [&](int& r, int& m, int& nf) {
+        if (m + 1 < nf) {
+            ++m;
+        } else if (r + 1 < nrow) {
+            ++r;
+            m = 0;
+            nf = row_n[r][tid];
+        }
+    };
+    // entry 0
+    int r0 = 0, m0 = 0, n0 = row_n[0][tid];
+    int s = row_s[0][tid];
+    vec_t<T> ps = C.pB[s];
+    eps_t<T> es = C.eB[s];
+    T bs = ps.w;
+    uint32_t ids = C.idB[s];
+    int t = C.fwd_j[(size_t)s * cap];
+    T w = C.fwd_w[(size_t)s * cap];
+    vec_t<T> pt = C.pB[t];
+    eps_t<T> et = C.eB[t];
+    T3<T> G = pair_gauss<T>(C.seed, step, (uint32_t)rep, ids, C.idB[t]);
+    // entry 1 (index only)
+    int r1 = r0, m1 = m0, n1 = n0;
+    advance(r1, m1, n1);
+    int s1 = row_s[r1][tid];
+    int t1 = C.fwd_j[(size_t)s1 * cap + m1];
+    T w1 = C.fwd_w[(size_t)s1 * cap + m1];
+    for (int k = 0; k < total; ++k) {
+        // index of entry k + 2
+        int r2 = r1, m2 = m1, n2 = n1;
+        advance(r2, m2, n2);
+        const int s2 = row_s[r2][tid];
+        const int t2 = C.fwd_j[(size_t)s2 * cap + m2];
+        const T w2 = C.fwd_w[(size_t)s2 * cap + m2];
+        // state of entry k + 1
+        const bool sw = s1 != s;
+        vec_t<T> pt1 = C.pB[t1];
+        eps_t<T> et1 = C.eB[t1];
+        const uint32_t idt1 = C.idB[t1];
+        vec_t<T> ps1 = ps;
+        eps_t<T> es1 = es;
+        uint32_t ids1 = ids;
+        if (sw) {
+            ps1 = C.pB[s1];
+            es1 = C.eB[s1];
+            ids1 = C.idB[s1];
+        }
+        // pair map of entry k
+        ssa_pair_map(C, R, ps, es, bs, pt, et, w, G, dt, amp0);
+        C.pB[t] = pt;
+        C.eB[t] = et;
+        if (t1 == t) {
+            pt1 = pt;
+            et1 = et;
+        }
+        // Gaussian of entry k + 1
+        const T3<T> G1 = pair_gauss<T>(C.seed, step, (uint32_t)rep, ids1, idt1);
+        if (sw) {
+            ps.w = bs;
+            C.pB[s] = ps;
+            C.eB[s] = es;
+            if (s1 == t) {
+                ps1 = pt;
+                es1 = et;
+            }
+            ps = ps1;
+            es = es1;
+            bs = ps1.w;
+            ids = ids1;
+            s = s1;
+        }
+        t = t1; w = w1; pt = pt1; et = et1; G = G1;
+        r1 = r2; m1 = m2; n1 = n2; s1 = s2; t1 = t2; w1 = w2;
+    }
+    ps.w = bs;
+    C.pB[s] = ps;
+    C.eB[s] = es;
 }
 
 template <class T>

@@ -64,7 +64,8 @@ _lib = None
 EXPORTS = ["dpde_create", "dpde_set_state", "dpde_get_state", "dpde_step", "dpde_sync",
            "dpde_observables", "dpde_get_step", "dpde_destroy", "dpde_last_error",
            "dpde_debug_philox", "dpde_debug_gaussian", "dpde_step_profiled", "dpde_get_cells",
-           "dpde_checkpoint", "dpde_restore", "dpde_observables_noalloc", "dpde_noalloc_last_error"]
+           "dpde_checkpoint", "dpde_restore", "dpde_observables_noalloc", "dpde_noalloc_last_error",
+           "dpde_step_launches"]
 PHASES = ["kick_drift", "scan", "gather", "force", "ssa", "sweep1", "sweep2", "other"]
 
 
@@ -96,6 +97,7 @@ def lib():
         L.dpde_checkpoint.argtypes = [vp, vp, C.POINTER(C.c_uint64)]
         L.dpde_restore.argtypes = [vp, vp, C.c_uint64]
         L.dpde_get_cells.argtypes = [vp, C.POINTER(C.c_int32)]
+        L.dpde_step_launches.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64)]
         L.dpde_step_profiled.argtypes = [vp, C.c_int64, C.c_double, C.c_int32, dp]
         L.dpde_debug_philox.argtypes = [C.c_int64, u32p, u32p, u32p]
         L.dpde_debug_gaussian.argtypes = [C.c_int64, C.c_uint64, u32p, u32p, u32p, u32p,
@@ -148,6 +150,13 @@ def dpde_step_profiled(h, n, dt, scheme) -> dict:
     _check(h, lib().dpde_step_profiled(h, int(n), float(dt), SCHEMES.get(scheme, scheme),
                                        ms.ctypes.data_as(C.POINTER(C.c_double))))
     return dict(zip(PHASES, ms.tolist()))
+
+
+def dpde_step_launches(h, scheme) -> int:
+    """Kernel launches in one step of `scheme`."""
+    out = C.c_int64(0)
+    _check(h, lib().dpde_step_launches(h, SCHEMES.get(scheme, scheme), C.byref(out)))
+    return int(out.value)
 
 
 def dpde_sync(h):
@@ -256,6 +265,9 @@ class System:
         out = np.empty((self.N, 3), np.int32)
         _check(self.h, lib().dpde_get_cells(self.h, out.ctypes.data_as(C.POINTER(C.c_int32))))
         return out
+
+    def step_launches(self, scheme) -> int:
+        return dpde_step_launches(self.h, scheme)
 
     def step(self, n, dt, scheme, use_graph=True):
         dpde_step(self.h, n, dt, scheme, use_graph)

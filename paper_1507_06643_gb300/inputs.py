@@ -110,6 +110,14 @@ def large_n4m(precision: str = "mixed") -> Workload:
                     steps=1000, seed=1003, precision=precision)
 
 
+def medium_n1m(precision: str = "mixed") -> Workload:
+    """The large fluid at a quarter of its size: N=1,000,000 at density 3
+    (L ~ 69.3), C_v=50; Hybrid domains 11x11x11 (6^3 cells each). Small
+    enough for detailed kernel captures, larger than L2."""
+    return Workload("medium_n1m", [ReplicaSpec(1_000_000, cubic_box(1_000_000), 50.0, 1.0, (11, 11, 11))],
+                    steps=1000, seed=1006, precision=precision)
+
+
 def shock_40x40x800(precision: str = "mixed") -> Workload:
     """Box 40 x 40 x 800 at density 3 (3.84M particles), periodic in all
     directions, halves moving at +-2 along z on a kT=1 Maxwellian, C_v=100,
@@ -141,6 +149,7 @@ WORKLOADS = {
     "plain_n1000": plain_n1000,
     "equilibrium_n108000": equilibrium_n108000,
     "large_n4m": large_n4m,
+    "medium_n1m": medium_n1m,
     "shock_40x40x800": shock_40x40x800,
     "batched_256": batched_256,
 }

@@ -99,7 +99,7 @@ def test_parity_plain_n1000(precision, scheme):
     (2500, (9.3, 9.3, 9.7), (3, 3, 3)),
     (6000, (12.6, 12.6, 12.6), (1, 1, 1)),   # one domain too large for shared memory
 ])
-@pytest.mark.parametrize("scheme", ["SER", "HYBRID"])
+@pytest.mark.parametrize("scheme", ["SER", "HYBRID", "SSA"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_parity_sizes(n, box, bricks, scheme, precision):
     specs = [(n, box, 50.0, 1.0, bricks)]
@@ -208,6 +208,31 @@ def test_momentum_is_conserved():
     P1 = S.observables()[0]
     for k in ("Px", "Py", "Pz"):
         assert abs(P1[k] - P0[k]) < 1e-9
+
+
+@pytest.mark.parametrize("box,bricks", [((6.93, 6.93, 6.93), (2, 2, 2)), ((5.0, 7.3, 7.1), (1, 2, 3)),
+                                        ((7.0, 10.5, 13.6), (2, 3, 1))])
+def test_ssa_launches_follow_colour_classes(box, bricks):
+    """One SSA launch per non-empty colour class: P = 3, 3, 2 colours along
+    x, y, z, plus one per leftover cell (k mod P) along a periodic domain
+    axis."""
+    from paper_1507_06643_gb300 import dpde
+    n = int(DENSE * np.prod(box))
+    S = dpde.System(dpde.make_params(precision="mixed"), [dpde.make_replica(n, box, 50.0, bricks)])
+
+    def classes(whole):
+        out = 1
+        for d, P in enumerate((3, 3, 2)):
+            nc = bricks[d] * int(np.floor(box[d] / bricks[d]))
+            k = nc if whole else nc // bricks[d]
+            periodic = whole or bricks[d] == 1
+            out *= min(P, k) + (k % P if periodic and k >= P else 0)
+        return out
+
+    ser, hyb, ssa = (S.step_launches(x) for x in ("SER", "HYBRID", "SSA"))
+    assert hyb - ser == classes(False)
+    assert ssa - (ser - 1) == classes(True)    # SSA: one copy-back in place of the two sweeps
+    S.close()
 
 
 # ---- errors -------------------------------------------------------------------------

@@ -170,7 +170,7 @@ def test_ssa_order_covers_each_pair_once(ora, bricks):
 
 @pytest.mark.parametrize("bricks,box", [((1, 1, 1), (6.934, 7.5, 9.7)), ((2, 2, 2), (6.934, 7.5, 9.7)),
                                         ((1, 2, 3), (6.934, 7.5, 9.7)), ((3, 1, 1), (7.5, 4.2, 5.3)),
-                                        ((2, 1, 1), (4.1, 3.4, 5.3))])
+                                        ((2, 1, 1), (4.1, 3.4, 5.3)), ((1, 1, 1), (3.2, 4.4, 3.3))])
 @pytest.mark.parametrize("whole_box", [False, True])
 def test_ssa_order_colour_classes_are_independent(ora, bricks, box, whole_box):
     """The sequence is a run of colour classes; inside one class the pairs of
@@ -187,10 +187,10 @@ def test_ssa_order_colour_classes_are_independent(ora, bricks, box, whole_box):
 
     def colour(c):
         out = []
-        for d in range(3):
+        for d, P in enumerate((3, 3, 2)):
             l = c[d] % dom_k[d]
-            full = 3 * (dom_k[d] // 3)
-            out.append(3 + l - full if periodic[d] and l >= full else l % 3)
+            full = P * (dom_k[d] // P)
+            out.append(P + l - full if periodic[d] and l >= full else l % P)
         return (out[2], out[1], out[0])
 
     seq = ora.ssa_order(rep, 1.0, q, whole_box=whole_box)
