@@ -358,17 +358,17 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     h->nbr_cap = (int)std::ceil(3.0 * mean_nbr) + 32;
     const size_t vsz = h->mixed ? sizeof(float4) : sizeof(d4);
     const size_t esz = h->mixed ? sizeof(ff) : sizeof(double);
-    // force tiles: halo of (TILE_EDGE + 2)^3 cells staged up to 1.15x the mean + 64
+    // force tiles: halo of (TILE_EDGE + 2)^3 cells staged up to 1.08x the mean
+    // + 64 (over 3 standard deviations of a uniform fluid's halo count)
     {
-        const size_t vsz0 = vsz;
         const int hcmax = (TILE_EDGE + 2) * (TILE_EDGE + 2) * (TILE_EDGE + 2);
-        const size_t thead =
-            (((size_t)(3 * hcmax + 1 + 66 + HIT_BUF * TILE_THREADS) * sizeof(int)) + 31) & ~(size_t)31;
-        const size_t tper = vsz0 + 2 * sizeof(unsigned short);
+        const size_t thead = h->mixed ? tile_head_bytes<float>() : tile_head_bytes<double>();
+        const size_t tper = h->mixed ? tile_per_particle<float>() : tile_per_particle<double>();
         const double mean_halo = per_cell_max * hcmax;
         const size_t smem_limit = 200 * 1024;
-        h->hcap = (int)std::min<double>(std::min<double>(1.15 * mean_halo + 64.0, 65535.0),
+        h->hcap = (int)std::min<double>(std::min<double>(1.08 * mean_halo + 64.0, 65535.0),
                                         (double)((smem_limit - thead) / tper));
+        h->hcap &= ~3;   // keeps the arrays after the positions 16-byte aligned
         h->tile_smem = 32 + thead + (size_t)h->hcap * tper;
     }
     // SSA colour classes (cell colours of the SSA order, per axis l mod P

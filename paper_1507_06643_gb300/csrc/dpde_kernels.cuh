@@ -388,14 +388,12 @@ struct PairOut {
     int nn = 0, nf = 0;
 };
 
-// one neighbour j (global slot) of i at separation d with |d|^2 = r2
-struct NoiseKey {
-    uint32_t step, rep, id_i;
-};
-
+// one neighbour j (global slot) of i at separation d with |d|^2 = r2; fwd
+// tells whether j is a forward neighbour of i, cross whether j's brick
+// differs from i's
 template <class T, int LM>
-__device__ __forceinline__ void force_hit(const Ctx<T>& C, int i, int j, uint32_t id_j, const NoiseKey& nk,
-                                          int seg, bool cross, T dx, T dy, T dz, T r2, PairOut<T>& o) {
+__device__ __forceinline__ void force_hit(const Ctx<T>& C, int i, int j, bool fwd, bool cross, T dx, T dy, T dz,
+                                          T r2, PairOut<T>& o) {
     const size_t N = (size_t)C.N;
     T w = T(1);
     if (r2 > T(0)) {
@@ -410,7 +408,7 @@ __device__ __forceinline__ void force_hit(const Ctx<T>& C, int i, int j, uint32_
             C.nbr_w[(size_t)o.nn * N + i] = w;
         }
         ++o.nn;
-    } else if ((LM == LIST_CROSS || LM == LIST_FWD) && (seg > 13 || (seg == 13 && j > i))) {
+    } else if ((LM == LIST_CROSS || LM == LIST_FWD) && fwd) {
         if (o.nf < C.nbr_cap) {
             const size_t at = (size_t)i * C.nbr_cap + o.nf;
             C.fwd_j[at] = j;
@@ -451,7 +449,6 @@ __device__ void force_one_global(const Ctx<T>& C, int i, T half_dt, int kick) {
     const T lx = cell_len<T>(R, 0), ly = cell_len<T>(R, 1), lz = cell_len<T>(R, 2);
     const int* bt = brick_tab(C.tab, R);
     const int bx = __ldg(bt + cx), by = __ldg(bt + nx + cy), bz = __ldg(bt + nx + ny + cz);
-    const NoiseKey nk{(uint32_t)*C.step, (uint32_t)C.rep_of_slot[i], id_of(qi)};
     PairOut<T> o;
     for (int sg = 0; sg < 27; ++sg) {
         const int dxc = sg % 3 - 1, dyc = (sg / 3) % 3 - 1, dzc = sg / 9 - 1;
@@ -468,7 +465,7 @@ __device__ void force_one_global(const Ctx<T>& C, int i, T half_dt, int kick) {
             const vec_t<T> qj = C.qB[j];
             const T ddx = (qi.x - qj.x) - sx, ddy = (qi.y - qj.y) - sy, ddz = (qi.z - qj.z) - sz;
             const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-            if (r2 < C.rc2) force_hit<T, LM>(C, i, j, id_of(qj), nk, sg, cross, ddx, ddy, ddz, r2, o);
+            if (r2 < C.rc2) force_hit<T, LM>(C, i, j, sg > 13 || (sg == 13 && j > i), cross, ddx, ddy, ddz, r2, o);
         }
     }
     force_finish<T, LM>(C, i, half_dt, kick, o);
@@ -476,16 +473,31 @@ __device__ void force_one_global(const Ctx<T>& C, int i, T half_dt, int kick) {
 
 // Tiled force pass: one block per tile of (up to) 6 x 6 x 6 cells. The tile
 // and its one-cell halo are staged in shared memory in x-fastest halo-cell
-// order, so the three x-cells of each (dy, dz) neighbour row of a particle
-// form one contiguous range. The lanes of a warp walk the 9 rows in step;
-// the candidate loop only records hits (halo index and segment) in a
-// per-thread shared buffer, and a second loop over the hits computes forces
-// and lists -- so the costly part runs once per neighbour, not once per
-// candidate of the slowest lane. Halos larger than hcap fall back to the
+// order (slot order inside a cell), with positions shifted into one frame
+// centred on the tile, so a separation is a plain difference and the three
+// x-cells of each (dy, dz) neighbour row of a particle form one contiguous
+// range. In this layout j is a forward neighbour of i (later segment, or
+// same cell and later slot) exactly when its halo index is larger, and the
+// rows are visited in (segment, slot) order. The lanes of a warp walk the 9
+// rows in step; the candidate loop only records hits (16-bit halo indices)
+// in a per-thread shared buffer, and a second loop over the hits computes
+// forces and lists -- so the costly part runs once per neighbour, not once
+// per candidate of the slowest lane. Halos larger than hcap fall back to the
 // global path.
 constexpr int TILE_THREADS = 256;
 constexpr int TILE_EDGE = 6;
-constexpr int HIT_BUF = 24;
+constexpr int HIT_BUF = 32;   // hits buffered per thread (flushed when full)
+
+template <class T>
+__host__ __device__ constexpr size_t tile_head_bytes() {
+    constexpr int HCMAX = (TILE_EDGE + 2) * (TILE_EDGE + 2) * (TILE_EDGE + 2);
+    return ((size_t)(3 * HCMAX + 1 + 66) * sizeof(int) + (size_t)HIT_BUF * TILE_THREADS * 2 + 31) & ~(size_t)31;
+}
+// shared bytes per staged halo particle: position, global slot, brick, own index
+template <class T>
+__host__ __device__ constexpr size_t tile_per_particle() {
+    return sizeof(vec_t<T>) + 2 * sizeof(int) + sizeof(unsigned short);
+}
 
 template <class T, int LM>
 __global__ void __launch_bounds__(TILE_THREADS) k_force_tile(Ctx<T> C, const int4* __restrict__ tile_org,
@@ -501,19 +513,19 @@ __global__ void __launch_bounds__(TILE_THREADS) k_force_tile(Ctx<T> C, const int
     const int HC = HX * HY * HZ;
     const int nx = R.nc[0], ny = R.nc[1], nz = R.nc[2];
     // shared layout (sized for HC <= (TILE_EDGE+2)^3):
-    //   hstart[HC+1] gstart[HC] hbrick[HC] rowoff[65] nown | hits[HIT_BUF][TILE_THREADS] |
-    //   q[hcap] hcell[hcap] own[hcap]
+    //   hstart[HC+1] gstart[HC] hbrick[HC] rowoff[65] nown | hits[HIT_BUF][TILE_THREADS] (u16) |
+    //   q[hcap] glob[hcap] brick[hcap] own[hcap]
     constexpr int HCMAX = (TILE_EDGE + 2) * (TILE_EDGE + 2) * (TILE_EDGE + 2);
     int* hstart = (int*)smem;
     int* gstart = hstart + HCMAX + 1;
     int* hbrick = gstart + HCMAX;
     int* rowoff = hbrick + HCMAX;
     int* nown = rowoff + 65;
-    unsigned* hits = (unsigned*)(nown + 1);
-    const size_t head = (((size_t)(3 * HCMAX + 1 + 66 + HIT_BUF * TILE_THREADS) * sizeof(int)) + 31) & ~(size_t)31;
-    vec* hq = (vec*)(smem + head);
-    unsigned short* hcell = (unsigned short*)(hq + hcap);
-    unsigned short* own = hcell + hcap;
+    unsigned short* hits = (unsigned short*)(nown + 1);
+    vec* hq = (vec*)(smem + tile_head_bytes<T>());
+    int* hglob = (int*)(hq + hcap);
+    int* hbr = hglob + hcap;
+    unsigned short* own = (unsigned short*)(hbr + hcap);
     const int* bt = brick_tab(C.tab, R);
     // 1. halo cells: global start, count, brick
     for (int h = threadIdx.x; h < HC; h += blockDim.x) {
@@ -542,13 +554,21 @@ __global__ void __launch_bounds__(TILE_THREADS) k_force_tile(Ctx<T> C, const int
     __syncthreads();
     const int H = hstart[HC];
     const bool staged = H <= hcap;
-    // 3. stage the halo particles; 4. own-row offsets
+    const T lx = cell_len<T>(R, 0), ly = cell_len<T>(R, 1), lz = cell_len<T>(R, 2);
+    // 3. stage the halo particles (tile frame); 4. own-row offsets
     if (staged) {
+        const int cxh = HX / 2, cyh = HY / 2, czh = HZ / 2;
         for (int h = threadIdx.x; h < HC; h += blockDim.x) {
             const int b = hstart[h], n = hstart[h + 1] - b, g = gstart[h];
+            const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+            const T ox = (T)(hx - cxh) * lx, oy = (T)(hy - cyh) * ly, oz = (T)(hz - czh) * lz;
+            const int br = hbrick[h];
             for (int k = 0; k < n; ++k) {
-                hq[b + k] = C.qB[g + k];
-                hcell[b + k] = (unsigned short)h;
+                vec qv = C.qB[g + k];
+                qv.x += ox; qv.y += oy; qv.z += oz;
+                hq[b + k] = qv;
+                hglob[b + k] = g + k;
+                hbr[b + k] = br;
             }
         }
     }
@@ -582,58 +602,68 @@ __global__ void __launch_bounds__(TILE_THREADS) k_force_tile(Ctx<T> C, const int
     }
     __syncthreads();
     // 5. each own particle: rows in step, hits recorded, then processed
-    const T lx = cell_len<T>(R, 0), ly = cell_len<T>(R, 1), lz = cell_len<T>(R, 2);
-    const uint32_t step = (uint32_t)*C.step;
     const int no = *nown;
-    unsigned* myhits = hits + threadIdx.x;
+    unsigned short* myhits = hits + threadIdx.x;
     for (int k0 = 0; k0 < no; k0 += blockDim.x) {
         const int k = k0 + threadIdx.x;
         const bool act = k < no;
         const int hi = act ? own[k] : 0;
-        const int hc = hcell[hi];
-        const int i = gstart[hc] + (hi - hstart[hc]);
         const vec qi = hq[hi];
-        const int hx = hc % HX, hy = (hc / HX) % HY, hz = hc / (HX * HY);
-        const int mybrick = hbrick[hc];
-        const NoiseKey nk{step, (uint32_t)org.x, id_of(qi)};
+        const int i = hglob[hi];
+        const int mybrick = hbr[hi];
+        // halo coordinates of i's cell, from its row base
+        int hc = 0;
+        {
+            // the own cell is found from the own-row table
+            int lo = 0, hi2 = nrow;   // row r: rowoff[r] <= k < rowoff[r + 1]
+            while (hi2 - lo > 1) {
+                const int mid = (lo + hi2) >> 1;
+                if (rowoff[mid] <= k) lo = mid;
+                else hi2 = mid;
+            }
+            const int h = ((lo / dim.y + 1) * HY + (lo % dim.y + 1)) * HX;
+            int cx = 1;
+            while (cx < dim.x && hstart[h + cx + 1] <= hi) ++cx;
+            hc = h + cx;
+        }
         PairOut<T> o;
         int nh = 0;
         auto flush = [&]() {
             for (int u = 0; u < nh; ++u) {
-                const unsigned e = myhits[u * TILE_THREADS];
-                const int hj = (int)(e & 0xffffu);
-                const int seg = (int)(e >> 16);
-                const int dxc = seg % 3 - 1, dyc = (seg / 3) % 3 - 1, dzc = seg / 9 - 1;
+                const int hj = myhits[u * TILE_THREADS];
                 const vec qj = hq[hj];
-                const T ddx = (qi.x - qj.x) - shift<T>(dxc, lx);
-                const T ddy = (qi.y - qj.y) - shift<T>(dyc, ly);
-                const T ddz = (qi.z - qj.z) - shift<T>(dzc, lz);
+                const T ddx = qi.x - qj.x, ddy = qi.y - qj.y, ddz = qi.z - qj.z;
                 const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                const int hcj = hcell[hj];
-                const int j = gstart[hcj] + (hj - hstart[hcj]);
-                force_hit<T, LM>(C, i, j, id_of(qj), nk, seg, hbrick[hcj] != mybrick, ddx, ddy, ddz, r2, o);
+                force_hit<T, LM>(C, i, hglob[hj], hj > hi, hbr[hj] != mybrick, ddx, ddy, ddz, r2, o);
             }
             nh = 0;
         };
+        auto near = [&](int j) {
+            const vec qj = hq[j];
+            const T ddx = qi.x - qj.x, ddy = qi.y - qj.y, ddz = qi.z - qj.z;
+            return ddx * ddx + ddy * ddy + ddz * ddz < C.rc2 && j != hi;
+        };
+        auto record = [&](int j) {
+            if (nh == HIT_BUF) flush();
+            myhits[nh * TILE_THREADS] = (unsigned short)j;
+            ++nh;
+        };
         for (int row = 0; row < 9; ++row) {
-            const int dyr = row % 3 - 1, dzr = row / 3 - 1;
-            const int base = ((hz + dzr) * HY + (hy + dyr)) * HX + hx - 1;
-            const int b1 = hstart[base + 1], b2 = hstart[base + 2];
+            const int base = hc + (row / 3 - 1) * HX * HY + (row % 3 - 1) * HX - 1;
             const int je = act ? hstart[base + 3] : 0;
-            const T sy = shift<T>(dyr, ly), sz = shift<T>(dzr, lz);
-            for (int j = act ? hstart[base] : 0; j < je; ++j) {
-                if (j == hi) continue;
-                const vec qj = hq[j];
-                const int dxc = (j >= b1) + (j >= b2) - 1;
-                const T ddx = (qi.x - qj.x) - shift<T>(dxc, lx);
-                const T ddy = (qi.y - qj.y) - sy;
-                const T ddz = (qi.z - qj.z) - sz;
-                if (ddx * ddx + ddy * ddy + ddz * ddz < C.rc2) {
-                    if (nh == HIT_BUF) flush();
-                    myhits[nh * TILE_THREADS] = (unsigned)j | ((unsigned)(3 * row + dxc + 1) << 16);
-                    ++nh;
+            int j = act ? hstart[base] : 0;
+            // four independent candidates per pass, hits kept in order
+            for (; j + 4 <= je; j += 4) {
+                const bool h0 = near(j), h1 = near(j + 1), h2 = near(j + 2), h3 = near(j + 3);
+                if (h0 | h1 | h2 | h3) {
+                    if (h0) record(j);
+                    if (h1) record(j + 1);
+                    if (h2) record(j + 2);
+                    if (h3) record(j + 3);
                 }
             }
+            for (; j < je; ++j)
+                if (near(j)) record(j);
         }
         flush();
         if (act) force_finish<T, LM>(C, i, half_dt, kick, o);
@@ -1001,16 +1031,20 @@ __global__ void k_obs_chunks(Ctx<T> C, const int* __restrict__ chunk_rep, const 
         acc[9] += (e <= 0.0) ? 1.0 : 0.0;
         acc[10] += fin ? 0.0 : 1.0;
         if (fin) {
-            double u = 0.0, lap = 0.0;
+            // per neighbour, in the step's precision: w = 1 - r/r_c and, for
+            // r > 0, the Laplacian term a/r_c - 2a w/r = 3a/r_c - 2a/r
+            T w2 = 0, inv_r = 0;
+            int npos = 0;
             for_each_neighbour(C, C.qA, i, qi, C.cA[i], R,
                                [&](int, const vec_t<T>&, T, T, T, T r2, bool) {
-                                   const double r = sqrt((double)r2);
-                                   const double w = 1.0 - r / (double)C.rc;
-                                   u += 0.5 * half_rc_a * w * w;   // each pair is seen twice
-                                   if (r > 0.0) lap += (double)C.a / (double)C.rc - 2.0 * (double)C.a * w / r;
+                                   const T ir = r2 > T(0) ? trsqrt(r2) : T(0);
+                                   const T w = T(1) - r2 * ir * C.inv_rc;
+                                   w2 += w * w;
+                                   inv_r += ir;
+                                   npos += r2 > T(0) ? 1 : 0;
                                });
-            acc[1] += u;
-            acc[8] += lap;
+            acc[1] += 0.5 * half_rc_a * (double)w2;   // each pair is seen twice
+            acc[8] += 3.0 * (double)C.a / (double)C.rc * npos - 2.0 * (double)C.a * (double)inv_r;
         }
     }
     __shared__ double sh[NTERMS][OBS_THREADS];

@@ -107,6 +107,43 @@ def test_parity_sizes(n, box, bricks, scheme, precision):
         break
 
 
+def slab_state(seed, L=12.0, rho=3.0, rho_slab=9.0, slab=4.0, float32=False):
+    """Uniform fluid at rho with a slab z < `slab` at rho_slab: cells there
+    hold ~3x the mean, so SSA chains overflow the per-cell row table and the
+    per-block Gaussian staging."""
+    rng = np.random.default_rng(seed)
+    n0 = int(rho * L ** 3)
+    n1 = int((rho_slab - rho) * L * L * slab)
+    q = np.concatenate([rng.random((n0, 3)) * L, rng.random((n1, 3)) * np.array([L, L, slab])])
+    n = len(q)
+    p = rng.standard_normal((n, 3))
+    p -= p.mean(axis=0)
+    e = 50.0 * (1 + 0.05 * rng.uniform(-1, 1, n))
+    if float32:
+        q = q.astype(np.float32).astype(np.float64)
+        q = np.where(q >= L, 0.0, q)
+        p = p.astype(np.float32).astype(np.float64)
+    return q, p, e
+
+
+@pytest.mark.parametrize("bricks", [(1, 1, 1), (2, 2, 2)])
+@pytest.mark.parametrize("scheme", ["HYBRID", "SSA"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_parity_dense_slab(precision, scheme, bricks):
+    compared = 0
+    for seed in range(31, 39):
+        state = slab_state(seed, float32=precision == "mixed")
+        specs = [(len(state[0]), (12.0, 12.0, 12.0), 50.0, 1.0, bricks)]
+        errs, flips, _, _ = run_both(specs, precision, scheme, 4, state=state)
+        if flips:
+            continue
+        assert max(errs.values()) < TOL[precision], (seed, errs)
+        compared += 1
+        if compared == 2:
+            break
+    assert compared >= 1
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("scheme", ["SER", "HYBRID", "SSA"])
 def test_parity_batched_replicas(precision, scheme):
