@@ -139,8 +139,9 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     S = dpde.System(prm, spec_reps, stream=stream.cuda_stream)
     S.set_state(q, p, e)
-    obs0 = S.observables()
     dt = w.dt
+    tuning = S.autotune(args.scheme, dt, 10) if not args.no_autotune else S.tuning()
+    obs0 = S.observables()
 
     S.step(args.warmup, dt, args.scheme)
     assert S.sync() == dpde.DPDE_OK
@@ -175,6 +176,7 @@ def run_ours(args):
     ph = torch.from_numpy(p).pin_memory()
     eh = torch.from_numpy(e).pin_memory()
     S2 = dpde.System(prm, spec_reps, stream=stream.cuda_stream)
+    S2.set_tuning(**{k: tuning[k] for k in ("tile_edge", "block", "ssa_block")})
     e2e_steps = args.e2e_steps
     S2.set_state(qh, ph, eh)
     torch.cuda.synchronize()
@@ -183,12 +185,16 @@ def run_ours(args):
         dpde.dpde_set_state(S2.h, qh, ph, eh, 0, False)
         S2.step(1, dt, args.scheme)
         rc = dpde.dpde_get_state(S2.h, qh, ph, eh, False)
-        assert rc == dpde.DPDE_OK
+        # a negative internal energy is a reported outcome of the scheme
+        # (state still advanced); anything else stops the run
+        if rc not in (dpde.DPDE_OK, dpde.DPDE_ERR_NEG_EPS):
+            raise RuntimeError(f"end-to-end step failed: {rc} {dpde.lib().dpde_last_error(S2.h).decode()}")
     e2e_s = time.perf_counter() - tt
+    e2e_status = rc
     S2.close()
     e2e = {"value": n_tot * world * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(q.nbytes + p.nbytes + e.nbytes),
-           "d2h_bytes_per_step": int(q.nbytes + p.nbytes + e.nbytes)}
+           "d2h_bytes_per_step": int(q.nbytes + p.nbytes + e.nbytes), "status": e2e_status}
 
     peaks, peak_src = measured_peaks()
     bound, work, unit = algorithmic_model(w, dom, phase_avg, w.precision)
@@ -213,7 +219,9 @@ def run_ours(args):
         "config": {"workload": w.name, "n": n_tot, "scheme": args.scheme, "precision": w.precision,
                    "dt": dt, "bricks": list(w.replicas[0].bricks), "l2": "inputs larger than L2 "
                    f"(state ~{n_tot * (48 if w.precision == 'mixed' else 104) / 1e6:.0f} MB)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "tuning": {k: tuning[k] for k in ("tile_edge", "block", "ssa_block")},
+                   "autotuned": not args.no_autotune},
         "e2e": e2e,
         "gpu_launches": None,
         "roofline": roofline,
@@ -223,14 +231,78 @@ def run_ours(args):
     }
     nlaunch = S.step_launches(args.scheme)
     out["gpu_launches"] = nlaunch * args.steps
+    S.close()
+    if args.fp64_steps > 0 and w.precision == "mixed":
+        f64 = fp64_run(args, spec_reps, w, q, p, e, stream)
+        out["fp64_gpu"] = f64
+        out["speedup_mixed_over_fp64"] = value / (f64["value"] * world)
+    if args.drift_steps > 0:
+        out["energy_drift"] = drift_run(args, stream)
     if rank == 0:
         out["clocks"] = clk.summary()
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(w, args.scheme, args.cpu_seconds)
         print(json.dumps(out))
-    S.close()
     if world > 1:
         tdist.destroy_process_group()
+
+
+def fp64_run(args, spec_reps, w, q, p, e, stream):
+    """The same workload and scheme with every quantity in double."""
+    import torch
+    from paper_1507_06643_gb300 import dpde
+    prm = dpde.make_params(w.mass, w.r_cut, w.a, w.sigma, w.seed, "fp64")
+    S = dpde.System(prm, spec_reps, stream=stream.cuda_stream)
+    S.set_state(q, p, e)
+    S.step(3, w.dt, args.scheme)
+    assert S.sync() == dpde.DPDE_OK
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    S.step(args.fp64_steps, w.dt, args.scheme)
+    t1.record(stream)
+    t1.synchronize()
+    ms = t0.elapsed_time(t1)
+    S.close()
+    return {"value": w.n_total * args.fp64_steps / (ms / 1e3), "unit": UNIT, "steps": args.fp64_steps,
+            "warmup": 3, "ms_per_step": ms / args.fp64_steps, "dtype": "f64"}
+
+
+def drift_run(args, stream):
+    """Total-energy drift on the N=108,000 equilibrium fluid: max over samples
+    every `every` steps of |E^n - E^0| / |E^0| after an equilibration, with
+    the mean kinetic and internal temperatures over the samples, in mixed
+    and FP64 modes (same seed and initial state)."""
+    from paper_1507_06643_gb300 import dpde, inputs
+    out = {"workload": "equilibrium_n108000", "scheme": args.scheme, "equilibration_steps": args.drift_equil,
+           "steps": args.drift_steps}
+    every = max(1, min(1000, args.drift_steps // 10))
+    for prec in ("mixed", "fp64"):
+        w = inputs.equilibrium_n108000(prec)
+        reps = [dpde.make_replica(x.n, x.box, x.cv, x.bricks) for x in w.replicas]
+        S = dpde.System(dpde.make_params(w.mass, w.r_cut, w.a, w.sigma, w.seed, prec), reps,
+                        stream=stream.cuda_stream)
+        q, p, e = inputs.workload_state(w)
+        S.set_state(q, p, e)
+        S.step(args.drift_equil, w.dt, args.scheme)
+        o0 = S.observables(check=True)[0]
+        E0, dev, tk, ti = o0["E"], 0.0, [], []
+        done = 0
+        t = time.perf_counter()
+        while done < args.drift_steps:
+            k = min(every, args.drift_steps - done)
+            S.step(k, w.dt, args.scheme)
+            done += k
+            o = S.observables(check=True)[0]
+            dev = max(dev, abs(o["E"] - E0) / abs(E0))
+            tk.append(o["Tkin"])
+            ti.append(o["Tint"])
+        el = time.perf_counter() - t
+        S.close()
+        out[prec] = {"max_rel_drift": dev, "final_rel_drift": abs(o["E"] - E0) / abs(E0),
+                     "mean_Tkin": float(np.mean(tk)), "mean_Tint": float(np.mean(ti)),
+                     "wall_s": el}
+    return out
 
 
 def oracle_sample(w, n_target: int):
@@ -315,6 +387,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=20,
+                    help="steps of the FP64 GPU run of the same workload (0: skip)")
+    ap.add_argument("--drift-steps", type=int, default=10000,
+                    help="measured steps of the energy-drift run on the 108k fluid (0: skip)")
+    ap.add_argument("--drift-equil", type=int, default=2000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

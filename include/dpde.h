@@ -320,6 +320,39 @@ const char* dpde_noalloc_last_error(void);
 int dpde_step_profiled(dpde_handle* h, int64_t n, double dt, int32_t scheme,
                        double* phase_ms);
 
+/* ---- tuning ---- */
+
+/* Launch parameters of a handle. None of them changes what is computed; the
+ * tile edge changes the float rounding of pair separations in the force pass
+ * (positions are shifted into a frame per tile), the block sizes change
+ * nothing in the results. */
+typedef struct dpde_tuning {
+    int32_t tile_edge;   /* force tile edge in cells, 2..8 (default 6)                */
+    int32_t block;       /* threads per block of the per-particle kernels: a multiple  */
+                         /* of 32 in 64..1024 (default 256)                           */
+    int32_t ssa_block;   /* threads per block of the SSA launches: 32, 64, 96 or 128   */
+                         /* (default 64)                                               */
+    int32_t reserved;    /* must be 0                                                  */
+    double ms_per_step;  /* dpde_autotune: measured ms per step of the result; else 0  */
+} dpde_tuning;
+
+/* Current tuning of the handle (host pointer). */
+int dpde_get_tuning(dpde_handle* h, dpde_tuning* out);
+
+/* Sets the tuning (host pointer; ms_per_step ignored). Waits for the handle's
+ * stream and drops the captured step graphs. DPDE_ERR_ARG for values outside
+ * the ranges above. */
+int dpde_set_tuning(dpde_handle* h, const dpde_tuning* t);
+
+/* Autotuner: times `steps` graph-replayed steps of `scheme` at `dt` (after
+ * one untimed replay) for each candidate -- tile edges 4..8, then per-particle block sizes
+ * 128, 256, 512, then SSA block sizes 32, 64, 128, each stage keeping the
+ * best so far -- on the handle's current state, restoring that state, its
+ * forces and its step counter after every trial; then applies the fastest
+ * tuning and writes it to *out (host pointer, may be NULL). The state after
+ * the call equals the state before it. Synchronous. steps in 1..1000. */
+int dpde_autotune(dpde_handle* h, int32_t scheme, double dt, int32_t steps, dpde_tuning* out);
+
 /* Number of kernel launches in one step of `scheme` (the kernel nodes of
  * the step's CUDA graph, captured here without being run; *launches, host
  * pointer). The count depends on the handle's geometry: the SSA part has one

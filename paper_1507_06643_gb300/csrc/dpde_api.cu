@@ -55,7 +55,12 @@ struct dpde_handle {
     int* col_cells[2] = {nullptr, nullptr};
     std::vector<int> col_off[2];   // NCOLOURS + 1 offsets into col_cells
     int hcap = 0;             // halo particles staged per force tile
+    int hcc = 0;              // halo cells per force tile, (tile_edge + 2)^3
     size_t tile_smem = 0;
+    double per_cell_max = 0;  // mean particles per cell of the densest replica
+    // tuning (dpde_set_tuning / dpde_autotune)
+    int tile_edge = TILE_EDGE;
+    int ssa_block = SSA_THREADS;
     uint32_t* idB = nullptr;
     int *key = nullptr, *tmp = nullptr, *cnt = nullptr, *start = nullptr, *bsum = nullptr;
     int *rep_of_slot = nullptr, *rep_of_cell = nullptr, *brick_rep = nullptr, *tab = nullptr;
@@ -151,10 +156,10 @@ template <class T>
 void enqueue_force(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T half_dt, int kick, int list) {
     const dim3 g(h->ntiles), blk(TILE_THREADS);
     switch (list) {
-    case LIST_ALL: k_force_tile<T, LIST_ALL><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap); break;
-    case LIST_CROSS: k_force_tile<T, LIST_CROSS><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap); break;
-    case LIST_FWD: k_force_tile<T, LIST_FWD><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap); break;
-    default: k_force_tile<T, LIST_NONE><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap); break;
+    case LIST_ALL: k_force_tile<T, LIST_ALL><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap, h->hcc); break;
+    case LIST_CROSS: k_force_tile<T, LIST_CROSS><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap, h->hcc); break;
+    case LIST_FWD: k_force_tile<T, LIST_FWD><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap, h->hcc); break;
+    default: k_force_tile<T, LIST_NONE><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap, h->hcc); break;
     }
 }
 
@@ -165,8 +170,8 @@ void enqueue_ssa(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_
     for (int k = 0; k < NCOLOURS; ++k) {
         const int n = off[k + 1] - off[k];
         if (n > 0)
-            k_ssa_colour<T><<<ceil_div(n, SSA_THREADS), SSA_THREADS, 0, st>>>(C, h->col_cells[whole] + off[k], n,
-                                                                            dt, sqrt_dt);
+            k_ssa_colour<T><<<ceil_div(n, h->ssa_block), h->ssa_block, ssa_smem_bytes(h->ssa_block), st>>>(
+                C, h->col_cells[whole] + off[k], n, dt, sqrt_dt);
     }
 }
 
@@ -196,6 +201,14 @@ void enqueue_step(dpde_handle* h, cudaStream_t st, double dt_d, int scheme) {
     else k_copy_back<T><<<nb, h->block, 0, st>>>(C);
     phase(h, st, DPDE_PHASE_SWEEP2, 1);
     k_step_inc<<<1, 1, 0, st>>>(h->d_step);
+}
+
+// Rebuilds the cell starts of the current A set (already in (cell, id) order)
+// without moving anything: the keys come from the stored cells and the
+// gather into B is the identity. Needed after the A set is written directly.
+void enqueue_rebin(dpde_handle* h, cudaStream_t st) {
+    if (h->mixed) enqueue_sort<float>(h, make_ctx<float>(h), st, 0.f, 0.f, 0);
+    else enqueue_sort<double>(h, make_ctx<double>(h), st, 0.0, 0.0, 0);
 }
 
 void enqueue_step_any(dpde_handle* h, cudaStream_t st, double dt, int scheme) {
@@ -256,6 +269,57 @@ void free_all(dpde_handle* h) {
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
+// Force tiles of edge `edge` cells over every replica, their halo staging
+// capacity (1.08x the mean halo count of the densest replica + 64, over 3
+// standard deviations of a uniform fluid's count) and shared memory size.
+int set_tiles(dpde_handle* h, int edge) {
+    std::vector<int4> torg, tdim;
+    for (int r = 0; r < h->R; ++r) {
+        const RepInfo& I = h->info[r];
+        for (int z0 = 0; z0 < I.nc[2]; z0 += edge)
+            for (int y0 = 0; y0 < I.nc[1]; y0 += edge)
+                for (int x0 = 0; x0 < I.nc[0]; x0 += edge) {
+                    torg.push_back(make_int4(r, x0, y0, z0));
+                    tdim.push_back(make_int4(std::min(edge, I.nc[0] - x0), std::min(edge, I.nc[1] - y0),
+                                             std::min(edge, I.nc[2] - z0), 0));
+                }
+    }
+    const int hcc = (edge + 2) * (edge + 2) * (edge + 2);
+    const size_t thead = tile_head_bytes(hcc);
+    const size_t tper = h->mixed ? tile_per_particle<float>() : tile_per_particle<double>();
+    const double mean_halo = h->per_cell_max * hcc;
+    const size_t smem_limit = 200 * 1024;
+    int hcap = (int)std::min<double>(std::min<double>(1.08 * mean_halo + 64.0, 65535.0),
+                                     (double)((smem_limit - thead) / tper));
+    hcap &= ~3;   // keeps the arrays after the positions 16-byte aligned
+    const size_t smem = 32 + thead + (size_t)hcap * tper;
+    if (h->tile_org) cudaFree(h->tile_org);
+    if (h->tile_dim) cudaFree(h->tile_dim);
+    h->tile_org = h->tile_dim = nullptr;
+    CK(h, cudaMalloc(&h->tile_org, sizeof(int4) * std::max<size_t>(1, torg.size())));
+    CK(h, cudaMalloc(&h->tile_dim, sizeof(int4) * std::max<size_t>(1, tdim.size())));
+    CK(h, cudaMemcpy(h->tile_org, torg.data(), sizeof(int4) * torg.size(), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->tile_dim, tdim.data(), sizeof(int4) * tdim.size(), cudaMemcpyHostToDevice));
+    const int sm = (int)smem;
+    if (h->mixed) {
+        CK(h, cudaFuncSetAttribute(k_force_tile<float, LIST_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        CK(h, cudaFuncSetAttribute(k_force_tile<float, LIST_ALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        CK(h, cudaFuncSetAttribute(k_force_tile<float, LIST_CROSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        CK(h, cudaFuncSetAttribute(k_force_tile<float, LIST_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    } else {
+        CK(h, cudaFuncSetAttribute(k_force_tile<double, LIST_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        CK(h, cudaFuncSetAttribute(k_force_tile<double, LIST_ALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        CK(h, cudaFuncSetAttribute(k_force_tile<double, LIST_CROSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        CK(h, cudaFuncSetAttribute(k_force_tile<double, LIST_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    }
+    h->ntiles = (int)torg.size();
+    h->hcc = hcc;
+    h->hcap = hcap;
+    h->tile_smem = smem;
+    h->tile_edge = edge;
+    return DPDE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -278,7 +342,6 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     long long N = 0, ncells = 0, nbricks = 0;
     const int CHUNK = 4096;
     std::vector<int> chunk_rep, chunk_begin, chunk_end, rep_chunk_begin(1, 0), tabs, brick_rep;
-    std::vector<int4> torg, tdim;
     double rho_max = 0.0, per_cell_max = 0.0;
     for (int r = 0; r < n_replicas; ++r) {
         const dpde_replica& d = replicas[r];
@@ -324,13 +387,6 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         for (int a = 0; a < 3; ++a)
             for (int c = 0; c < I.nc[a]; ++c) tabs.push_back(c / I.k[a]);
         for (int b = 0; b < nbr; ++b) brick_rep.push_back(r);
-        for (int z0 = 0; z0 < I.nc[2]; z0 += TILE_EDGE)
-            for (int y0 = 0; y0 < I.nc[1]; y0 += TILE_EDGE)
-                for (int x0 = 0; x0 < I.nc[0]; x0 += TILE_EDGE) {
-                    torg.push_back(make_int4(r, x0, y0, z0));
-                    tdim.push_back(make_int4(std::min(TILE_EDGE, I.nc[0] - x0), std::min(TILE_EDGE, I.nc[1] - y0),
-                                             std::min(TILE_EDGE, I.nc[2] - z0), 0));
-                }
         per_cell_max = std::max(per_cell_max, (double)d.n / (double)(I.nc[0] * I.nc[1] * I.nc[2]));
         rho_max = std::max(rho_max, (double)d.n / (d.box[0] * d.box[1] * d.box[2]));
         h->info.push_back(I);
@@ -352,25 +408,12 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     h->ncells = (int)ncells;
     h->nbricks = (int)nbricks;
     h->nchunks = (int)chunk_rep.size();
-    h->ntiles = (int)torg.size();
+    h->per_cell_max = per_cell_max;
     // neighbour-list capacity: 3x the mean neighbour count of the densest replica, + 32
     const double mean_nbr = 4.0 / 3.0 * M_PI * rho_max * P.r_cut * P.r_cut * P.r_cut;
     h->nbr_cap = (int)std::ceil(3.0 * mean_nbr) + 32;
     const size_t vsz = h->mixed ? sizeof(float4) : sizeof(d4);
     const size_t esz = h->mixed ? sizeof(ff) : sizeof(double);
-    // force tiles: halo of (TILE_EDGE + 2)^3 cells staged up to 1.08x the mean
-    // + 64 (over 3 standard deviations of a uniform fluid's halo count)
-    {
-        const int hcmax = (TILE_EDGE + 2) * (TILE_EDGE + 2) * (TILE_EDGE + 2);
-        const size_t thead = h->mixed ? tile_head_bytes<float>() : tile_head_bytes<double>();
-        const size_t tper = h->mixed ? tile_per_particle<float>() : tile_per_particle<double>();
-        const double mean_halo = per_cell_max * hcmax;
-        const size_t smem_limit = 200 * 1024;
-        h->hcap = (int)std::min<double>(std::min<double>(1.08 * mean_halo + 64.0, 65535.0),
-                                        (double)((smem_limit - thead) / tper));
-        h->hcap &= ~3;   // keeps the arrays after the positions 16-byte aligned
-        h->tile_smem = 32 + thead + (size_t)h->hcap * tper;
-    }
     // SSA colour classes (cell colours of the SSA order, per axis l mod P
     // with P = 3, 3, 2 along x, y, z, and colours P, P + 1 for the last
     // k mod P cells of a periodic domain axis), for brick domains (m = 0)
@@ -444,8 +487,6 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     CKC(cudaMalloc(&h->fwd_j, sizeof(int) * n1 * (size_t)h->nbr_cap));
     CKC(cudaMalloc(&h->fwd_w, tsz * n1 * (size_t)h->nbr_cap));
     CKC(cudaMalloc(&h->fwd_n, sizeof(int) * n1));
-    CKC(cudaMalloc(&h->tile_org, sizeof(int4) * torg.size()));
-    CKC(cudaMalloc(&h->tile_dim, sizeof(int4) * tdim.size()));
     CKC(cudaMalloc(&h->key, sizeof(int) * n1));
     CKC(cudaMalloc(&h->tmp, sizeof(int) * n1));
     CKC(cudaMalloc(&h->cnt, sizeof(int) * 2 * c1));
@@ -477,8 +518,6 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         CKC(cudaMemcpy(h->rep_of_cell, roc.data(), sizeof(int) * c1, cudaMemcpyHostToDevice));
         CKC(cudaMemcpy(h->brick_rep, brick_rep.data(), sizeof(int) * brick_rep.size(), cudaMemcpyHostToDevice));
         CKC(cudaMemcpy(h->tab, tabs.data(), sizeof(int) * tabs.size(), cudaMemcpyHostToDevice));
-        CKC(cudaMemcpy(h->tile_org, torg.data(), sizeof(int4) * torg.size(), cudaMemcpyHostToDevice));
-        CKC(cudaMemcpy(h->tile_dim, tdim.data(), sizeof(int4) * tdim.size(), cudaMemcpyHostToDevice));
         if (!chunk_rep.empty()) {
             CKC(cudaMemcpy(h->chunk_rep, chunk_rep.data(), sizeof(int) * chunk_rep.size(), cudaMemcpyHostToDevice));
             CKC(cudaMemcpy(h->chunk_begin, chunk_begin.data(), sizeof(int) * chunk_rep.size(), cudaMemcpyHostToDevice));
@@ -504,17 +543,12 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
                            cudaMemcpyHostToDevice));
     }
     {
-        const int sm = (int)h->tile_smem;
-        if (h->mixed) {
-            CKC(cudaFuncSetAttribute(k_force_tile<float, LIST_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-            CKC(cudaFuncSetAttribute(k_force_tile<float, LIST_ALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-            CKC(cudaFuncSetAttribute(k_force_tile<float, LIST_CROSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-            CKC(cudaFuncSetAttribute(k_force_tile<float, LIST_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-        } else {
-            CKC(cudaFuncSetAttribute(k_force_tile<double, LIST_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-            CKC(cudaFuncSetAttribute(k_force_tile<double, LIST_ALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-            CKC(cudaFuncSetAttribute(k_force_tile<double, LIST_CROSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-            CKC(cudaFuncSetAttribute(k_force_tile<double, LIST_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        const int rc = set_tiles(h, TILE_EDGE);
+        if (rc != DPDE_OK) {
+            const std::string msg = h->err;
+            free_all(h);
+            delete h;
+            return fail(nullptr, rc, msg);
         }
     }
 #undef CKC
@@ -614,6 +648,133 @@ int dpde_step(dpde_handle* h, int64_t n, double dt, int32_t scheme, int32_t use_
     }
     h->step += n;
     return DPDE_OK;
+}
+
+int dpde_get_tuning(dpde_handle* h, dpde_tuning* out) {
+    if (!h || !out) return DPDE_ERR_ARG;
+    out->tile_edge = h->tile_edge;
+    out->block = h->block;
+    out->ssa_block = h->ssa_block;
+    out->reserved = 0;
+    out->ms_per_step = 0.0;
+    return DPDE_OK;
+}
+
+int dpde_set_tuning(dpde_handle* h, const dpde_tuning* t) {
+    if (!h || !t) return DPDE_ERR_ARG;
+    if (t->tile_edge < 2 || t->tile_edge > TILE_EDGE_MAX || t->block < 64 || t->block > 1024 ||
+        t->block % 32 != 0 || t->ssa_block < 32 || t->ssa_block > SSA_THREADS_MAX || t->ssa_block % 32 != 0 ||
+        t->reserved != 0)
+        return fail(h, DPDE_ERR_ARG, "tuning out of range");
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    if (t->tile_edge != h->tile_edge) {
+        const int rc = set_tiles(h, t->tile_edge);
+        if (rc != DPDE_OK) return rc;
+    }
+    h->block = t->block;
+    h->ssa_block = t->ssa_block;
+    return DPDE_OK;
+}
+
+int dpde_autotune(dpde_handle* h, int32_t scheme, double dt, int32_t steps, dpde_tuning* out) {
+    if (!h) return DPDE_ERR_ARG;
+    if (scheme < DPDE_SER || scheme > DPDE_SSA || !(dt > 0) || !std::isfinite(dt) || steps < 1 || steps > 1000)
+        return fail(h, DPDE_ERR_ARG, "bad scheme, dt or steps");
+    dpde_tuning best{};
+    dpde_get_tuning(h, &best);
+    if (h->N == 0) {
+        if (out) *out = best;
+        return DPDE_OK;
+    }
+    // saved state: A set, forces, step counter
+    const size_t n = (size_t)h->N;
+    const size_t vsz = h->mixed ? sizeof(float4) : sizeof(d4);
+    const size_t esz = h->mixed ? sizeof(ff) : sizeof(double);
+    const size_t bytes = 3 * vsz * n + esz * n + sizeof(int) * n + sizeof(long long);
+    unsigned char* save = nullptr;
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMalloc(&save, bytes));
+    struct Piece { void* dev; size_t size; };
+    const Piece pieces[] = {{h->qA, vsz * n}, {h->pA, vsz * n}, {h->F, vsz * n}, {h->eA, esz * n},
+                            {h->cA, sizeof(int) * n}, {h->d_step, sizeof(long long)}};
+    auto copy_all = [&](bool to_save) -> cudaError_t {
+        size_t off = 0;
+        for (const Piece& pc : pieces) {
+            cudaError_t e = to_save ? cudaMemcpyAsync(save + off, pc.dev, pc.size, cudaMemcpyDeviceToDevice, h->stream)
+                                    : cudaMemcpyAsync(pc.dev, save + off, pc.size, cudaMemcpyDeviceToDevice, h->stream);
+            if (e != cudaSuccess) return e;
+            off += pc.size;
+        }
+        return cudaSuccess;
+    };
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int rc = DPDE_OK;
+    // one trial: the step captured as a graph (as dpde_step runs it), one
+    // untimed replay, then `steps` timed replays
+    auto trial = [&](const dpde_tuning& t, double& ms) -> int {
+        int r = dpde_set_tuning(h, &t);
+        if (r != DPDE_OK) return r;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ex = nullptr;
+        CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_step_any(h, h->cap_stream, dt, scheme);
+        CK(h, cudaStreamEndCapture(h->cap_stream, &g));
+        const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return cuda_fail(h, ie, "cudaGraphInstantiate");
+        cudaError_t e = cudaGraphLaunch(ex, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
+        for (int k = 0; k < steps && e == cudaSuccess; ++k) e = cudaGraphLaunch(ex, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        cudaGraphExecDestroy(ex);
+        if (e != cudaSuccess) return cuda_fail(h, e, "autotune trial");
+        float f = 0.f;
+        CK(h, cudaEventElapsedTime(&f, ev[0], ev[1]));
+        ms = (double)f / steps;
+        CK(h, copy_all(false));
+        CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        return DPDE_OK;
+    };
+    do {
+        if ((rc = (cudaEventCreate(&ev[0]) == cudaSuccess && cudaEventCreate(&ev[1]) == cudaSuccess)
+                      ? DPDE_OK : fail(h, DPDE_ERR_CUDA, "cudaEventCreate")) != DPDE_OK)
+            break;
+        if (copy_all(true) != cudaSuccess) { rc = fail(h, DPDE_ERR_CUDA, "saving the state"); break; }
+        double best_ms = 0.0;
+        if ((rc = trial(best, best_ms)) != DPDE_OK) break;
+        const int edges[] = {4, 5, 6, 7, 8}, blocks[] = {128, 256, 512}, ssa_blocks[] = {32, 64, 128};
+        for (int stage = 0; stage < 3 && rc == DPDE_OK; ++stage) {
+            const int* cand = stage == 0 ? edges : (stage == 1 ? blocks : ssa_blocks);
+            const int nc = stage == 0 ? 5 : 3;
+            dpde_tuning base = best;
+            for (int c = 0; c < nc && rc == DPDE_OK; ++c) {
+                dpde_tuning t = base;
+                (stage == 0 ? t.tile_edge : (stage == 1 ? t.block : t.ssa_block)) = cand[c];
+                double ms = 0.0;
+                rc = trial(t, ms);
+                if (rc == DPDE_OK && ms < best_ms) {
+                    best_ms = ms;
+                    best = t;
+                }
+            }
+        }
+        if (rc != DPDE_OK) break;
+        best.ms_per_step = 0.0;
+        if ((rc = dpde_set_tuning(h, &best)) != DPDE_OK) break;
+        enqueue_rebin(h, h->stream);
+        if (cudaGetLastError() != cudaSuccess) { rc = fail(h, DPDE_ERR_CUDA, "rebinning the state"); break; }
+        best.ms_per_step = best_ms;
+    } while (false);
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(save);
+    if (rc == DPDE_OK && out) *out = best;
+    return rc;
 }
 
 int dpde_step_launches(dpde_handle* h, int32_t scheme, int64_t* launches) {
@@ -766,6 +927,9 @@ int dpde_restore(dpde_handle* h, const void* buf, uint64_t size) {
     long long s = (long long)hd.step;
     CK(h, cudaMemcpy(h->d_step, &s, sizeof(long long), cudaMemcpyHostToDevice));
     CK(h, cudaMemset(h->d_status, 0, sizeof(unsigned)));
+    if (N > 0) enqueue_rebin(h, h->stream);
+    CK(h, cudaGetLastError());
+    CK(h, cudaStreamSynchronize(h->stream));
     h->step = s;
     return DPDE_OK;
 }

@@ -485,13 +485,14 @@ __device__ void force_one_global(const Ctx<T>& C, int i, T half_dt, int kick) {
 // per candidate of the slowest lane. Halos larger than hcap fall back to the
 // global path.
 constexpr int TILE_THREADS = 256;
-constexpr int TILE_EDGE = 6;
-constexpr int HIT_BUF = 32;   // hits buffered per thread (flushed when full)
+constexpr int TILE_EDGE = 6;       // default tile edge (cells); the autotuner picks 4..8
+constexpr int TILE_EDGE_MAX = 8;
+constexpr int HIT_BUF = 32;        // hits buffered per thread (flushed when full)
 
-template <class T>
-__host__ __device__ constexpr size_t tile_head_bytes() {
-    constexpr int HCMAX = (TILE_EDGE + 2) * (TILE_EDGE + 2) * (TILE_EDGE + 2);
-    return ((size_t)(3 * HCMAX + 1 + 66) * sizeof(int) + (size_t)HIT_BUF * TILE_THREADS * 2 + 31) & ~(size_t)31;
+// shared bytes before the staged particles, for halo cell capacity hcc
+// ((edge + 2)^3): hstart, gstart, hbrick, rowoff (edge^2 + 1 <= 65), nown, hits
+__host__ __device__ constexpr size_t tile_head_bytes(int hcc) {
+    return ((size_t)(3 * hcc + 1 + 66) * sizeof(int) + (size_t)HIT_BUF * TILE_THREADS * 2 + 31) & ~(size_t)31;
 }
 // shared bytes per staged halo particle: position, global slot, brick, own index
 template <class T>
@@ -502,7 +503,7 @@ __host__ __device__ constexpr size_t tile_per_particle() {
 template <class T, int LM>
 __global__ void __launch_bounds__(TILE_THREADS) k_force_tile(Ctx<T> C, const int4* __restrict__ tile_org,
                                                              const int4* __restrict__ tile_dim, T half_dt,
-                                                             int kick, int hcap) {
+                                                             int kick, int hcap, int hcc) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((size_t)smem_raw + 31) & ~(size_t)31);
     using vec = vec_t<T>;
@@ -512,17 +513,16 @@ __global__ void __launch_bounds__(TILE_THREADS) k_force_tile(Ctx<T> C, const int
     const int HX = dim.x + 2, HY = dim.y + 2, HZ = dim.z + 2;
     const int HC = HX * HY * HZ;
     const int nx = R.nc[0], ny = R.nc[1], nz = R.nc[2];
-    // shared layout (sized for HC <= (TILE_EDGE+2)^3):
-    //   hstart[HC+1] gstart[HC] hbrick[HC] rowoff[65] nown | hits[HIT_BUF][TILE_THREADS] (u16) |
+    // shared layout (sized for HC <= hcc = (edge + 2)^3):
+    //   hstart[hcc+1] gstart[hcc] hbrick[hcc] rowoff[65] nown | hits[HIT_BUF][TILE_THREADS] (u16) |
     //   q[hcap] glob[hcap] brick[hcap] own[hcap]
-    constexpr int HCMAX = (TILE_EDGE + 2) * (TILE_EDGE + 2) * (TILE_EDGE + 2);
     int* hstart = (int*)smem;
-    int* gstart = hstart + HCMAX + 1;
-    int* hbrick = gstart + HCMAX;
-    int* rowoff = hbrick + HCMAX;
+    int* gstart = hstart + hcc + 1;
+    int* hbrick = gstart + hcc;
+    int* rowoff = hbrick + hcc;
     int* nown = rowoff + 65;
     unsigned short* hits = (unsigned short*)(nown + 1);
-    vec* hq = (vec*)(smem + tile_head_bytes<T>());
+    vec* hq = (vec*)(smem + tile_head_bytes(hcc));
     int* hglob = (int*)(hq + hcap);
     int* hbr = hglob + hcap;
     unsigned short* own = (unsigned short*)(hbr + hcap);
@@ -540,15 +540,26 @@ __global__ void __launch_bounds__(TILE_THREADS) k_force_tile(Ctx<T> C, const int
         hbrick[h] = __ldg(bt + x) | (__ldg(bt + nx + y) << 10) | (__ldg(bt + nx + ny + z) << 20);
     }
     __syncthreads();
-    // 2. exclusive scan of the halo counts (HC <= 512: two values per thread)
+    // 2. exclusive scan of the halo counts (a run of up to 4 per thread, HC <= 1000)
     {
         __shared__ int sh[32];
-        const int h0 = 2 * threadIdx.x, h1 = h0 + 1;
-        const int v0 = h0 < HC ? hstart[h0] : 0, v1 = h1 < HC ? hstart[h1] : 0;
+        const int per = (HC + TILE_THREADS - 1) / TILE_THREADS;
+        const int h0 = threadIdx.x * per;
+        int v[4] = {0, 0, 0, 0}, run = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (u < per && h0 + u < HC) {
+                v[u] = hstart[h0 + u];
+                run += v[u];
+            }
         int total;
-        const int ex = block_exclusive_scan(v0 + v1, sh, total);
-        if (h0 < HC) hstart[h0] = ex;
-        if (h1 < HC) hstart[h1] = ex + v0;
+        int ex = block_exclusive_scan(run, sh, total);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (u < per && h0 + u < HC) {
+                hstart[h0 + u] = ex;
+                ex += v[u];
+            }
         if (threadIdx.x == 0) hstart[HC] = total;
     }
     __syncthreads();
@@ -818,7 +829,8 @@ __global__ void k_sem(Ctx<T> C, T dt, T sqrt_dt) {
 // later particle of the cell may itself be t); those take the new values
 // from registers.
 // ---------------------------------------------------------------------------
-constexpr int SSA_THREADS = 64;
+constexpr int SSA_THREADS = 64;      // default block size; the autotuner picks 32..128
+constexpr int SSA_THREADS_MAX = 128;
 constexpr int SSA_ROWS = 20;     // rows per cell held in the shared row table
 constexpr int NCOLOURS = 75;     // (2 + 1) x (3 + 2) x (3 + 2) cell colours
 
@@ -878,11 +890,16 @@ __device__ void ssa_chain_plain(const Ctx<T>& C, const RepInfo& R, int rep, int 
     }
 }
 
+// dynamic shared memory of k_ssa_colour: two row tables [SSA_ROWS][block]
+__host__ __device__ constexpr size_t ssa_smem_bytes(int block) { return (size_t)2 * SSA_ROWS * block * sizeof(int); }
+
 template <class T>
-__global__ void __launch_bounds__(SSA_THREADS) k_ssa_colour(Ctx<T> C, const int* __restrict__ cells, int ncol,
-                                                            T dt, T sqrt_dt) {
-    __shared__ int row_s[SSA_ROWS][SSA_THREADS];   // slot of each non-empty row
-    __shared__ int row_n[SSA_ROWS][SSA_THREADS];   // its entry count
+__global__ void __launch_bounds__(SSA_THREADS_MAX) k_ssa_colour(Ctx<T> C, const int* __restrict__ cells,
+                                                                int ncol, T dt, T sqrt_dt) {
+    extern __shared__ int ssa_rows[];
+    const int bdim = blockDim.x;
+    int* row_s = ssa_rows;                    // [r * bdim + tid]: slot of each non-empty row
+    int* row_n = ssa_rows + SSA_ROWS * bdim;    //                 its entry count
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= ncol) return;
     const int tid = threadIdx.x;
@@ -893,8 +910,8 @@ __global__ void __launch_bounds__(SSA_THREADS) k_ssa_colour(Ctx<T> C, const int*
         const int nf = C.fwd_n[s];
         if (nf > 0) {
             if (nrow < SSA_ROWS) {
-                row_s[nrow][tid] = s;
-                row_n[nrow][tid] = nf;
+                row_s[nrow * bdim + tid] = s;
+                row_n[nrow * bdim + tid] = nf;
             }
             ++nrow;
             total += nf;
@@ -917,12 +934,12 @@ __global__ void __launch_bounds__(SSA_THREADS) k_ssa_colour(Ctx<T> C, const int*
         } else if (r + 1 < nrow) {
             ++r;
             m = 0;
-            nf = row_n[r][tid];
+            nf = row_n[r * bdim + tid];
         }
     };
     // entry 0
-    int r0 = 0, m0 = 0, n0 = row_n[0][tid];
-    int s = row_s[0][tid];
+    int r0 = 0, m0 = 0, n0 = row_n[tid];
+    int s = row_s[tid];
     vec_t<T> ps = C.pB[s];
     eps_t<T> es = C.eB[s];
     T bs = ps.w;
@@ -935,14 +952,14 @@ __global__ void __launch_bounds__(SSA_THREADS) k_ssa_colour(Ctx<T> C, const int*
     // entry 1 (index only)
     int r1 = r0, m1 = m0, n1 = n0;
     advance(r1, m1, n1);
-    int s1 = row_s[r1][tid];
+    int s1 = row_s[r1 * bdim + tid];
     int t1 = C.fwd_j[(size_t)s1 * cap + m1];
     T w1 = C.fwd_w[(size_t)s1 * cap + m1];
     for (int k = 0; k < total; ++k) {
         // index of entry k + 2
         int r2 = r1, m2 = m1, n2 = n1;
         advance(r2, m2, n2);
-        const int s2 = row_s[r2][tid];
+        const int s2 = row_s[r2 * bdim + tid];
         const int t2 = C.fwd_j[(size_t)s2 * cap + m2];
         const T w2 = C.fwd_w[(size_t)s2 * cap + m2];
         // state of entry k + 1

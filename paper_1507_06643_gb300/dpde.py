@@ -60,12 +60,20 @@ class dpde_obs(C.Structure):
         return d
 
 
+class dpde_tuning(C.Structure):
+    _fields_ = [("tile_edge", C.c_int32), ("block", C.c_int32), ("ssa_block", C.c_int32),
+                ("reserved", C.c_int32), ("ms_per_step", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 _lib = None
 EXPORTS = ["dpde_create", "dpde_set_state", "dpde_get_state", "dpde_step", "dpde_sync",
            "dpde_observables", "dpde_get_step", "dpde_destroy", "dpde_last_error",
            "dpde_debug_philox", "dpde_debug_gaussian", "dpde_step_profiled", "dpde_get_cells",
            "dpde_checkpoint", "dpde_restore", "dpde_observables_noalloc", "dpde_noalloc_last_error",
-           "dpde_step_launches"]
+           "dpde_step_launches", "dpde_get_tuning", "dpde_set_tuning", "dpde_autotune"]
 PHASES = ["kick_drift", "scan", "gather", "force", "ssa", "sweep1", "sweep2", "other"]
 
 
@@ -98,6 +106,9 @@ def lib():
         L.dpde_restore.argtypes = [vp, vp, C.c_uint64]
         L.dpde_get_cells.argtypes = [vp, C.POINTER(C.c_int32)]
         L.dpde_step_launches.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64)]
+        L.dpde_get_tuning.argtypes = [vp, C.POINTER(dpde_tuning)]
+        L.dpde_set_tuning.argtypes = [vp, C.POINTER(dpde_tuning)]
+        L.dpde_autotune.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, C.POINTER(dpde_tuning)]
         L.dpde_step_profiled.argtypes = [vp, C.c_int64, C.c_double, C.c_int32, dp]
         L.dpde_debug_philox.argtypes = [C.c_int64, u32p, u32p, u32p]
         L.dpde_debug_gaussian.argtypes = [C.c_int64, C.c_uint64, u32p, u32p, u32p, u32p,
@@ -157,6 +168,36 @@ def dpde_step_launches(h, scheme) -> int:
     out = C.c_int64(0)
     _check(h, lib().dpde_step_launches(h, SCHEMES.get(scheme, scheme), C.byref(out)))
     return int(out.value)
+
+
+def dpde_get_step(h) -> int:
+    out = C.c_int64(0)
+    _check(h, lib().dpde_get_step(h, C.byref(out)))
+    return int(out.value)
+
+
+def dpde_get_tuning(h) -> dict:
+    t = dpde_tuning()
+    _check(h, lib().dpde_get_tuning(h, C.byref(t)))
+    return t.as_dict()
+
+
+def dpde_set_tuning(h, tile_edge=None, block=None, ssa_block=None):
+    t = dpde_tuning()
+    _check(h, lib().dpde_get_tuning(h, C.byref(t)))
+    if tile_edge is not None:
+        t.tile_edge = int(tile_edge)
+    if block is not None:
+        t.block = int(block)
+    if ssa_block is not None:
+        t.ssa_block = int(ssa_block)
+    _check(h, lib().dpde_set_tuning(h, C.byref(t)))
+
+
+def dpde_autotune(h, scheme, dt, steps=3) -> dict:
+    t = dpde_tuning()
+    _check(h, lib().dpde_autotune(h, SCHEMES.get(scheme, scheme), float(dt), int(steps), C.byref(t)))
+    return t.as_dict()
 
 
 def dpde_sync(h):
@@ -268,6 +309,15 @@ class System:
 
     def step_launches(self, scheme) -> int:
         return dpde_step_launches(self.h, scheme)
+
+    def tuning(self) -> dict:
+        return dpde_get_tuning(self.h)
+
+    def set_tuning(self, **kw):
+        dpde_set_tuning(self.h, **kw)
+
+    def autotune(self, scheme, dt, steps=3) -> dict:
+        return dpde_autotune(self.h, scheme, dt, steps)
 
     def step(self, n, dt, scheme, use_graph=True):
         dpde_step(self.h, n, dt, scheme, use_graph)

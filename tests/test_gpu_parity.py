@@ -204,11 +204,15 @@ def test_checkpoint_restart_and_graph_are_bit_exact(precision, scheme):
     B.step(4, 0.01, scheme, use_graph=False)
     blob = B.checkpoint()
     mid = B.get_state()
+    obs_mid = B.observables()[0]
     C = dpde.System(prm, rep)
     C.restore(blob)
+    assert C.observables()[0] == obs_mid          # a fresh handle: cell starts rebuilt
     C.step(6, 0.01, scheme, use_graph=True)
     for x, y in zip(a, C.get_state()):
         assert np.array_equal(x, y)
+    C.restore(blob)                                 # a stepped handle: stale cell starts replaced
+    assert C.observables()[0] == obs_mid
     D = dpde.System(prm, rep)
     D.set_state(*mid, step=4)
     D.step(6, 0.01, scheme, use_graph=True)
@@ -269,6 +273,81 @@ def test_ssa_launches_follow_colour_classes(box, bricks):
     ser, hyb, ssa = (S.step_launches(x) for x in ("SER", "HYBRID", "SSA"))
     assert hyb - ser == classes(False)
     assert ssa - (ser - 1) == classes(True)    # SSA: one copy-back in place of the two sweeps
+    S.close()
+
+
+# ---- tuning -------------------------------------------------------------------------
+
+def _run_tuned(precision, tuning, steps=5, scheme="HYBRID"):
+    from paper_1507_06643_gb300 import dpde
+    specs = [(3000, (cube(3000),) * 3, 50.0, 1.0, (2, 2, 2))]
+    q, p, e = make_state(specs, 77, precision == "mixed")
+    S = dpde.System(dpde.make_params(precision=precision), [dpde.make_replica(*specs[0][:3], (2, 2, 2))])
+    if tuning:
+        S.set_tuning(**tuning)
+    S.set_state(q, p, e)
+    S.step(steps, 0.01, scheme)
+    out = S.get_state()
+    S.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_block_sizes_do_not_change_results(precision):
+    ref = _run_tuned(precision, None)
+    for t in ({"block": 128, "ssa_block": 32}, {"block": 512, "ssa_block": 128}, {"block": 64, "ssa_block": 96}):
+        got = _run_tuned(precision, t)
+        for a, b in zip(ref, got):
+            assert np.array_equal(a, b), t
+
+
+@pytest.mark.parametrize("edge", [2, 4, 5, 8])
+def test_tile_edge_changes_rounding_only(edge):
+    ref = _run_tuned("fp64", None)
+    got = _run_tuned("fp64", {"tile_edge": edge})
+    assert rel_err(got[1], ref[1]) < 1e-12 and rel_err(got[2], ref[2]) < 1e-12
+
+
+def test_autotune_keeps_the_state():
+    from paper_1507_06643_gb300 import dpde
+    specs = [(20000, (cube(20000),) * 3, 50.0, 1.0, (3, 3, 3))]
+    q, p, e = make_state(specs, 8, True)
+    S = dpde.System(dpde.make_params(precision="mixed"), [dpde.make_replica(*specs[0][:3], (3, 3, 3))])
+    S.set_state(q, p, e)
+    S.step(2, 0.01, "HYBRID")
+    before = S.get_state()
+    obs_before = S.observables()[0]
+    step0 = dpde.dpde_get_step(S.h)
+    t = S.autotune("HYBRID", 0.01, 2)
+    assert t["tile_edge"] in (4, 5, 6, 7, 8) and t["block"] in (128, 256, 512)
+    assert t["ssa_block"] in (32, 64, 128) and t["ms_per_step"] > 0
+    assert S.tuning()["tile_edge"] == t["tile_edge"]
+    after = S.get_state()
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    assert dpde.dpde_get_step(S.h) == step0
+    assert S.observables()[0] == obs_before
+    # stepping on continues like an untuned handle switched to the same tile edge
+    S.step(2, 0.01, "HYBRID")
+    got = S.get_state()
+    R = dpde.System(dpde.make_params(precision="mixed"), [dpde.make_replica(*specs[0][:3], (3, 3, 3))])
+    R.set_state(q, p, e)
+    R.step(2, 0.01, "HYBRID")
+    R.set_tuning(tile_edge=t["tile_edge"])
+    R.step(2, 0.01, "HYBRID")
+    for a, b in zip(got, R.get_state()):
+        assert np.array_equal(a, b)
+    S.close()
+    R.close()
+
+
+def test_bad_tuning_rejected():
+    from paper_1507_06643_gb300 import dpde
+    S = dpde.System(dpde.make_params(precision="mixed"), [dpde.make_replica(300, (cube(300),) * 3, 50.0)])
+    for kw in ({"tile_edge": 1}, {"tile_edge": 9}, {"block": 48}, {"block": 2048}, {"ssa_block": 256},
+               {"ssa_block": 48}):
+        with pytest.raises(dpde.DPDEError):
+            S.set_tuning(**kw)
     S.close()
 
 
