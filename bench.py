@@ -108,16 +108,45 @@ def workload_and_scheme(args):
     return w
 
 
-def algorithmic_model(w, phase: str, phases_ms: dict, precision: str):
-    """Algorithmic work of one launch of the dominant phase (see the design doc,
-    'Roofline'): unique pairs x operations per pair for the FD sweeps and the
-    SSA pass (ALU-bound), bytes for the memory-bound sort/force phases."""
+# Lane operations per unique pair (counted from the kernels' formulas; see
+# the roofline section of the design notes): one Gaussian triple = Philox4x32-10
+# (~80 INT) + Box-Muller (~100: 2 log, 2 sqrt, sincospi, cospi, scaling);
+# SSA pair map ~130 (2 expm1, 1 div, 1 sqrt, momenta, dK, two compensated eps
+# updates, two beta divisions); SER sweep 1 ~40, sweep 2 ~55 pair arithmetic.
+OPS_GAUSS = 180.0
+OPS_PER_PAIR = {"ssa": OPS_GAUSS + 130.0, "sweep1": OPS_GAUSS + 40.0, "sweep2": OPS_GAUSS + 55.0}
+
+
+def pair_counts(w):
+    """Unique pairs per step of the workload at uniform density: all pairs,
+    and those inside one brick (pairs uniform in the cutoff sphere have
+    E|dx_d| = 3 r_c / 8, so a pair crosses a brick face along d with
+    probability ~ 3 r_c / (8 b_d) for brick side b_d)."""
+    total = intra = 0.0
+    for r in w.replicas:
+        rho = r.n / (r.box[0] * r.box[1] * r.box[2])
+        pairs = r.n * 0.5 * (4.0 / 3.0) * math.pi * rho * w.r_cut ** 3
+        f = 1.0
+        for d in range(3):
+            b = r.box[d] / r.bricks[d]
+            f *= max(0.0, 1.0 - 0.375 * w.r_cut / b) if r.bricks[d] > 1 else 1.0
+        total += pairs
+        intra += pairs * f
+    return total, intra
+
+
+def algorithmic_model(w, phase: str, scheme: str, precision: str):
+    """Algorithmic work of the dominant phase in one step: unique pairs x lane
+    operations per pair for the SSA and SER phases (ALU-bound), bytes for the
+    memory-bound sort / force phases."""
     n = w.n_total
-    pairs_unique = n * 2.0 * math.pi * 3.0 / 3.0  # (4/3 pi rho r_c^3)/2 per particle
+    total, intra = pair_counts(w)
+    pairs = {"ssa": intra if scheme == "HYBRID" else total,
+             "sweep1": total - intra if scheme == "HYBRID" else total}
+    pairs["sweep2"] = pairs["sweep1"]
     state_bytes = 16 if precision == "mixed" else 32
-    if phase in ("sweep1", "sweep2", "ssa"):
-        ops = {"sweep1": 170.0, "sweep2": 185.0, "ssa": 230.0}[phase]
-        return "alu", pairs_unique * ops, "Gop/s"
+    if phase in OPS_PER_PAIR:
+        return "alu", pairs[phase] * OPS_PER_PAIR[phase], "Gop/s"
     if phase == "force":
         return "hbm", n * (state_bytes * 4.0), "GB/s"
     return "hbm", n * (state_bytes * 4.0 + 8 * 2 + 12), "GB/s"
@@ -140,6 +169,8 @@ def run_ours(args):
     S = dpde.System(prm, spec_reps, stream=stream.cuda_stream)
     S.set_state(q, p, e)
     dt = w.dt
+    # tune on a relaxed state: the first steps from the random start differ
+    S.step(args.warmup, dt, args.scheme)
     tuning = S.autotune(args.scheme, dt, 10) if not args.no_autotune else S.tuning()
     obs0 = S.observables()
 
@@ -182,7 +213,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     tt = time.perf_counter()
     for _ in range(e2e_steps):
-        dpde.dpde_set_state(S2.h, qh, ph, eh, 0, False)
+        try:
+            dpde.dpde_set_state(S2.h, qh, ph, eh, 0, False)
+        except dpde.DPDEError as err:   # input with eps <= 0: loaded and reported
+            if err.code != dpde.DPDE_ERR_NEG_EPS:
+                raise
         S2.step(1, dt, args.scheme)
         rc = dpde.dpde_get_state(S2.h, qh, ph, eh, False)
         # a negative internal energy is a reported outcome of the scheme
@@ -197,7 +232,7 @@ def run_ours(args):
            "d2h_bytes_per_step": int(q.nbytes + p.nbytes + e.nbytes), "status": e2e_status}
 
     peaks, peak_src = measured_peaks()
-    bound, work, unit = algorithmic_model(w, dom, phase_avg, w.precision)
+    bound, work, unit = algorithmic_model(w, dom, args.scheme, w.precision)
     dom_s = phase_avg[dom] / 1e3
     achieved = work / dom_s / 1e9
     if bound == "alu":
@@ -227,6 +262,7 @@ def run_ours(args):
         "roofline": roofline,
         "phase_ms": phase_avg,
         "energy": {"rel_drift_over_timed_steps": drift, "steps": args.steps + args.warmup,
+                   "after_steps": args.warmup,
                    "status": status},
     }
     nlaunch = S.step_launches(args.scheme)
@@ -286,7 +322,7 @@ def drift_run(args, stream):
         S.set_state(q, p, e)
         S.step(args.drift_equil, w.dt, args.scheme)
         o0 = S.observables(check=True)[0]
-        E0, dev, tk, ti = o0["E"], 0.0, [], []
+        E0, dev, tk, ti, Es = o0["E"], 0.0, [], [], [o0["E"]]
         done = 0
         t = time.perf_counter()
         while done < args.drift_steps:
@@ -295,13 +331,18 @@ def drift_run(args, stream):
             done += k
             o = S.observables(check=True)[0]
             dev = max(dev, abs(o["E"] - E0) / abs(E0))
+            Es.append(o["E"])
             tk.append(o["Tkin"])
             ti.append(o["Tint"])
         el = time.perf_counter() - t
         S.close()
         out[prec] = {"max_rel_drift": dev, "final_rel_drift": abs(o["E"] - E0) / abs(E0),
                      "mean_Tkin": float(np.mean(tk)), "mean_Tint": float(np.mean(ti)),
-                     "wall_s": el}
+                     "wall_s": el, "E": Es}
+    # precision-induced part: both runs share the initial state and the noise
+    em, ef = np.asarray(out["mixed"].pop("E")), np.asarray(out["fp64"].pop("E"))
+    out["max_rel_drift_mixed_minus_fp64"] = float(np.max(np.abs((em - em[0]) - (ef - ef[0]))) / abs(ef[0]))
+    out["sample_every"] = every
     return out
 
 
