@@ -356,7 +356,7 @@ int dpde_autotune(dpde_handle* h, int32_t scheme, double dt, int32_t steps, dpde
 /* Number of kernel launches in one step of `scheme` (the kernel nodes of
  * the step's CUDA graph, captured here without being run; *launches, host
  * pointer). The count depends on the handle's geometry: the SSA part has one
- * launch per non-empty cell colour class. No device work; the handle's state
+ * launch drawing the Gaussians, then one per non-empty cell colour class. No device work; the handle's state
  * and step counter are unchanged. DPDE_ERR_ARG for a bad scheme. */
 int dpde_step_launches(dpde_handle* h, int32_t scheme, int64_t* launches);
 

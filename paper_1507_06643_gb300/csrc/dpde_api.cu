@@ -46,7 +46,7 @@ struct dpde_handle {
     cudaStream_t cap_stream = nullptr;
     // device buffers
     void *qA = nullptr, *pA = nullptr, *qB = nullptr, *pB = nullptr, *F = nullptr, *dp = nullptr;
-    void *eA = nullptr, *eB = nullptr, *nbr_w = nullptr, *fwd_w = nullptr;
+    void *eA = nullptr, *eB = nullptr, *nbr_w = nullptr, *fwd_w = nullptr, *fwd_g = nullptr;
     int *cA = nullptr, *cB = nullptr, *nbr_j = nullptr, *nbr_n = nullptr, *fwd_j = nullptr, *fwd_n = nullptr;
     int4 *tile_org = nullptr, *tile_dim = nullptr;
     int ntiles = 0;
@@ -111,7 +111,7 @@ Ctx<T> make_ctx(dpde_handle* h) {
     C.key = h->key; C.tmp = h->tmp;
     C.count = h->cnt; C.fill = h->cnt + h->ncells; C.start = h->start;
     C.nbr_j = h->nbr_j; C.nbr_w = (T*)h->nbr_w; C.nbr_n = h->nbr_n; C.nbr_cap = h->nbr_cap;
-    C.fwd_j = h->fwd_j; C.fwd_w = (T*)h->fwd_w; C.fwd_n = h->fwd_n;
+    C.fwd_j = h->fwd_j; C.fwd_w = (T*)h->fwd_w; C.fwd_g = (vec_t<T>*)h->fwd_g; C.fwd_n = h->fwd_n;
     C.rep_of_slot = h->rep_of_slot; C.rep_of_cell = h->rep_of_cell;
     C.brick_rep = h->brick_rep; C.tab = h->tab;
     C.reps = h->d_reps; C.step = h->d_step; C.status = h->d_status;
@@ -163,10 +163,12 @@ void enqueue_force(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T half_dt, 
     }
 }
 
-// The SSA sequence: one launch per non-empty colour class, in colour order.
+// The SSA sequence: the Gaussians of every forward entry, then one launch per
+// non-empty colour class, in colour order.
 template <class T>
 void enqueue_ssa(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_dt, int whole) {
     const std::vector<int>& off = h->col_off[whole];
+    k_ssa_gauss<T><<<ceil_div(h->N, 256), 256, 0, st>>>(C);
     for (int k = 0; k < NCOLOURS; ++k) {
         const int n = off[k + 1] - off[k];
         if (n > 0)
@@ -259,7 +261,7 @@ void free_all(dpde_handle* h) {
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
     void* bufs[] = {h->qA, h->pA, h->qB, h->pB, h->F, h->dp, h->eA, h->eB, h->nbr_w, h->cA, h->cB, h->nbr_j,
-                    h->nbr_n, h->fwd_j, h->fwd_w, h->fwd_n, h->tile_org, h->tile_dim, h->col_cells[0], h->col_cells[1], h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
+                    h->nbr_n, h->fwd_j, h->fwd_w, h->fwd_g, h->fwd_n, h->tile_org, h->tile_dim, h->col_cells[0], h->col_cells[1], h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
                     h->rep_of_cell, h->brick_rep, h->tab, h->chunk_rep, h->chunk_begin, h->chunk_end,
                     h->rep_chunk_begin, h->partial, h->obs_out, h->d_reps, h->d_step, h->d_status,
                     h->staging, h->cells_out};
@@ -438,9 +440,11 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
             }
             for (int z = 0; z < I.nc[2]; ++z)
                 for (int y = 0; y < I.nc[1]; ++y)
-                    for (int x = 0; x < I.nc[0]; ++x)
-                        cls[(col[2][z] * 5 + col[1][y]) * 5 + col[0][x]].push_back(I.cell_off + tx[x] + ty[y] +
-                                                                                   tz[z]);
+                    for (int x = 0; x < I.nc[0]; ++x) {
+                        const int k = (col[2][z] * 5 + col[1][y]) * 5 + col[0][x];
+                        const int c = I.cell_off + tx[x] + ty[y] + tz[z];
+                        cls[k].push_back(c);
+                    }
         }
         h->col_off[m].assign(1, 0);
         for (auto& v : cls) {
@@ -486,6 +490,7 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     CKC(cudaMalloc(&h->nbr_n, sizeof(int) * n1));
     CKC(cudaMalloc(&h->fwd_j, sizeof(int) * n1 * (size_t)h->nbr_cap));
     CKC(cudaMalloc(&h->fwd_w, tsz * n1 * (size_t)h->nbr_cap));
+    CKC(cudaMalloc(&h->fwd_g, vsz * n1 * (size_t)h->nbr_cap));
     CKC(cudaMalloc(&h->fwd_n, sizeof(int) * n1));
     CKC(cudaMalloc(&h->key, sizeof(int) * n1));
     CKC(cudaMalloc(&h->tmp, sizeof(int) * n1));
@@ -787,10 +792,18 @@ int dpde_step_launches(dpde_handle* h, int32_t scheme, int64_t* launches) {
     enqueue_step_any(h, h->cap_stream, 0.01, scheme);
     CK(h, cudaStreamEndCapture(h->cap_stream, &g));
     size_t nodes = 0;
-    const cudaError_t e = cudaGraphGetNodes(g, nullptr, &nodes);
+    cudaError_t e = cudaGraphGetNodes(g, nullptr, &nodes);
+    std::vector<cudaGraphNode_t> list(nodes);
+    if (e == cudaSuccess && nodes > 0) e = cudaGraphGetNodes(g, list.data(), &nodes);
+    int64_t kernels = 0;
+    for (size_t k = 0; k < nodes && e == cudaSuccess; ++k) {
+        cudaGraphNodeType type;
+        e = cudaGraphNodeGetType(list[k], &type);
+        if (e == cudaSuccess && type == cudaGraphNodeTypeKernel) ++kernels;
+    }
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphGetNodes");
-    *launches = (int64_t)nodes;
+    *launches = kernels;
     return DPDE_OK;
 }
 

@@ -32,6 +32,7 @@ template <class T> struct Ctx {
     int* fwd_j;      // forward pairs of the SSA, particle-major rows [i * nbr_cap + k],
                      //   partner slots in SSA sequence order (segment, id)
     T* fwd_w;        //   w = 1 - r/r_cut of each entry
+    vec* fwd_g;      //   (G_it, w) of each entry, drawn before the SSA launches
     int* fwd_n;
     const int* rep_of_slot;
     const int* rep_of_cell;
@@ -812,19 +813,22 @@ __global__ void k_sem(Ctx<T> C, T dt, T sqrt_dt) {
 // SSA (Sec. III.A.2 and III.B.2): the pair map of Eq. (SSA_ij) -- the exact
 // OU transition of p_st at fixed gamma_st, after which eps_s and eps_t each
 // absorb -Delta K_st / 2 -- applied pair after pair in sequence order.
+//
+// The Gaussians do not depend on the state, so they are drawn first for every
+// forward entry by a fully parallel pass (k_ssa_gauss) and stored with the
+// entry's weight; the sequential part then only applies the maps.
+//
 // One launch per cell colour class; one thread per cell of the class. The
 // cells reached by the pairs of two cells of one class are disjoint, so the
-// threads touch disjoint particles and update set B in place.
-// A thread walks its cell's chain -- the forward rows of the cell's
-// particles s in slot (= id) order, concatenated -- as one flat loop, so the
-// lanes of a warp diverge only by chain length. (p_s, eps_s, beta_s) stay in
-// registers while s is current; the partner's updated (p_t, eps_t) goes back
-// to memory at once, with beta_t = C_v / eps_t in p_t.w, so p.w is the
-// current beta of every particle throughout.
-// The loop is software-pipelined so that only the pair map itself is on the
-// critical path: partner indices are loaded two entries ahead, the partner
-// state (and the next particle's state on a row change) and the Gaussian
-// one entry ahead. Loads issued ahead of a store can alias it only for the
+// threads touch disjoint particles and update set B in place. A thread walks
+// its cell's chain -- the forward rows of the cell's particles s in slot
+// (= id) order, concatenated -- as one flat loop, so the lanes of a warp
+// diverge only by chain length. (p_s, eps_s, beta_s) stay in registers while
+// s is current; the partner's updated (p_t, eps_t) goes back to memory at
+// once, with beta_t = C_v / eps_t in p_t.w, so p.w is the current beta of
+// every particle throughout. Partner indices are loaded two entries ahead,
+// the partner state (and the next particle's state on a row change) one
+// entry ahead. Loads issued ahead of a store can alias it only for the
 // partner t being updated (two rows of a cell may share a partner, and a
 // later particle of the cell may itself be t); those take the new values
 // from registers.
@@ -834,20 +838,62 @@ constexpr int SSA_THREADS_MAX = 128;
 constexpr int SSA_ROWS = 20;     // rows per cell held in the shared row table
 constexpr int NCOLOURS = 75;     // (2 + 1) x (3 + 2) x (3 + 2) cell colours
 
+// G of every forward entry, with its weight: (G_st, w) at [s * cap + m]. A
+// warp takes 32 consecutive particles and spreads their entries over its
+// lanes (a shuffle prefix sum of the row lengths gives each entry's owner).
+template <class T>
+__global__ void k_ssa_gauss(Ctx<T> C) {
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int base = s - lane;
+    const int nf = s < C.N ? C.fwd_n[s] : 0;
+    int incl = nf;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t step = (uint32_t)*C.step;
+    const size_t cap = (size_t)C.nbr_cap;
+    for (int f0 = 0; f0 < total; f0 += 32) {
+        const int f = f0 + lane;
+        // owner: the first lane whose inclusive prefix exceeds f
+        int lo = 0;
+#pragma unroll
+        for (int step2 = 16; step2 > 0; step2 >>= 1) {
+            const int v = __shfl_sync(0xffffffffu, incl, lo + step2 - 1);
+            if (v <= f) lo += step2;
+        }
+        const int excl = __shfl_sync(0xffffffffu, incl - nf, lo);
+        if (f < total) {
+            const int so = base + lo;
+            const size_t at = (size_t)so * cap + (f - excl);
+            const int t = C.fwd_j[at];
+            const T3<T> G = pair_gauss<T>(C.seed, step, (uint32_t)C.rep_of_slot[so], C.idB[so], C.idB[t]);
+            vec_t<T> g;
+            g.x = G.x; g.y = G.y; g.z = G.z; g.w = C.fwd_w[at];
+            C.fwd_g[at] = g;
+        }
+    }
+}
+
 // The pair map on (p_s, eps_s, beta_s) in registers and partner (p_t, eps_t)
-// with beta_t = p_t.w; returns the new partner state, beta in .w.
+// with beta_t = p_t.w, for the entry (G, w) = g; returns the new partner
+// state, beta in .w.
 template <class T>
 __device__ __forceinline__ void ssa_pair_map(const Ctx<T>& C, const RepInfo& R, vec_t<T>& ps, eps_t<T>& es,
-                                             T& bs, vec_t<T>& pt, eps_t<T>& et, T w, const T3<T>& G, T dt,
+                                             T& bs, vec_t<T>& pt, eps_t<T>& et, const vec_t<T>& g, T dt,
                                              T amp0) {
+    const T w = g.w;
     const T chi = w * w;
     const T gam = C.sig2_4 * (bs + pt.w);
     const T aa = T(2) * gam * chi * dt * C.inv_m;
     const T amp = (gam != T(0)) ? C.sigma * tsqrt(C.m * (-texpm1(T(-2) * aa)) / gam) : amp0 * w;
     const T em1 = texpm1(-aa);
-    const T Dx = T(0.5) * (em1 * (ps.x - pt.x) + amp * G.x);
-    const T Dy = T(0.5) * (em1 * (ps.y - pt.y) + amp * G.y);
-    const T Dz = T(0.5) * (em1 * (ps.z - pt.z) + amp * G.z);
+    const T Dx = T(0.5) * (em1 * (ps.x - pt.x) + amp * g.x);
+    const T Dy = T(0.5) * (em1 * (ps.y - pt.y) + amp * g.y);
+    const T Dz = T(0.5) * (em1 * (ps.z - pt.z) + amp * g.z);
     const T snx = ps.x + Dx, sny = ps.y + Dy, snz = ps.z + Dz;
     const T tnx = pt.x - Dx, tny = pt.y - Dy, tnz = pt.z - Dz;
     // kinetic-energy change of the stored momenta, halved
@@ -864,8 +910,7 @@ __device__ __forceinline__ void ssa_pair_map(const Ctx<T>& C, const RepInfo& R, 
 
 // Plain (unpipelined) chain, for cells with more than SSA_ROWS rows.
 template <class T>
-__device__ void ssa_chain_plain(const Ctx<T>& C, const RepInfo& R, int rep, int b, int e, uint32_t step, T dt,
-                                T amp0) {
+__device__ void ssa_chain_plain(const Ctx<T>& C, const RepInfo& R, int b, int e, T dt, T amp0) {
     const size_t cap = (size_t)C.nbr_cap;
     for (int s = b; s < e; ++s) {
         const int nf = C.fwd_n[s];
@@ -873,14 +918,12 @@ __device__ void ssa_chain_plain(const Ctx<T>& C, const RepInfo& R, int rep, int 
         vec_t<T> ps = C.pB[s];
         eps_t<T> es = C.eB[s];
         T bs = ps.w;
-        const uint32_t ids = C.idB[s];
         for (int m = 0; m < nf; ++m) {
             const int t = C.fwd_j[(size_t)s * cap + m];
-            const T w = C.fwd_w[(size_t)s * cap + m];
+            const vec_t<T> g = C.fwd_g[(size_t)s * cap + m];
             vec_t<T> pt = C.pB[t];
             eps_t<T> et = C.eB[t];
-            const T3<T> G = pair_gauss<T>(C.seed, step, (uint32_t)rep, ids, C.idB[t]);
-            ssa_pair_map(C, R, ps, es, bs, pt, et, w, G, dt, amp0);
+            ssa_pair_map(C, R, ps, es, bs, pt, et, g, dt, amp0);
             C.pB[t] = pt;
             C.eB[t] = et;
         }
@@ -898,8 +941,8 @@ __global__ void __launch_bounds__(SSA_THREADS_MAX) k_ssa_colour(Ctx<T> C, const 
                                                                 int ncol, T dt, T sqrt_dt) {
     extern __shared__ int ssa_rows[];
     const int bdim = blockDim.x;
-    int* row_s = ssa_rows;                    // [r * bdim + tid]: slot of each non-empty row
-    int* row_n = ssa_rows + SSA_ROWS * bdim;    //                 its entry count
+    int* row_s = ssa_rows;                      // [r * bdim + tid]: slot of each non-empty row
+    int* row_n = ssa_rows + SSA_ROWS * bdim;    //                   its entry count
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= ncol) return;
     const int tid = threadIdx.x;
@@ -918,12 +961,10 @@ __global__ void __launch_bounds__(SSA_THREADS_MAX) k_ssa_colour(Ctx<T> C, const 
         }
     }
     if (total == 0) return;
-    const int rep = C.rep_of_cell[c];
-    const RepInfo& R = C.reps[rep];
-    const uint32_t step = (uint32_t)*C.step;
+    const RepInfo& R = C.reps[C.rep_of_cell[c]];
     const T amp0 = T(2) * C.sigma * sqrt_dt;   // amplitude of the map as gamma -> 0
     if (nrow > SSA_ROWS) {
-        ssa_chain_plain(C, R, rep, b, e, step, dt, amp0);
+        ssa_chain_plain(C, R, b, e, dt, amp0);
         return;
     }
     const size_t cap = (size_t)C.nbr_cap;
@@ -938,53 +979,45 @@ __global__ void __launch_bounds__(SSA_THREADS_MAX) k_ssa_colour(Ctx<T> C, const 
         }
     };
     // entry 0
-    int r0 = 0, m0 = 0, n0 = row_n[tid];
     int s = row_s[tid];
     vec_t<T> ps = C.pB[s];
     eps_t<T> es = C.eB[s];
     T bs = ps.w;
-    uint32_t ids = C.idB[s];
     int t = C.fwd_j[(size_t)s * cap];
-    T w = C.fwd_w[(size_t)s * cap];
+    vec_t<T> g = C.fwd_g[(size_t)s * cap];
     vec_t<T> pt = C.pB[t];
     eps_t<T> et = C.eB[t];
-    T3<T> G = pair_gauss<T>(C.seed, step, (uint32_t)rep, ids, C.idB[t]);
-    // entry 1 (index only)
-    int r1 = r0, m1 = m0, n1 = n0;
+    // entry 1 (index and entry)
+    int r1 = 0, m1 = 0, n1 = row_n[tid];
     advance(r1, m1, n1);
     int s1 = row_s[r1 * bdim + tid];
     int t1 = C.fwd_j[(size_t)s1 * cap + m1];
-    T w1 = C.fwd_w[(size_t)s1 * cap + m1];
+    vec_t<T> g1 = C.fwd_g[(size_t)s1 * cap + m1];
     for (int k = 0; k < total; ++k) {
-        // index of entry k + 2
+        // index and entry of k + 2
         int r2 = r1, m2 = m1, n2 = n1;
         advance(r2, m2, n2);
         const int s2 = row_s[r2 * bdim + tid];
         const int t2 = C.fwd_j[(size_t)s2 * cap + m2];
-        const T w2 = C.fwd_w[(size_t)s2 * cap + m2];
+        const vec_t<T> g2 = C.fwd_g[(size_t)s2 * cap + m2];
         // state of entry k + 1
         const bool sw = s1 != s;
         vec_t<T> pt1 = C.pB[t1];
         eps_t<T> et1 = C.eB[t1];
-        const uint32_t idt1 = C.idB[t1];
         vec_t<T> ps1 = ps;
         eps_t<T> es1 = es;
-        uint32_t ids1 = ids;
         if (sw) {
             ps1 = C.pB[s1];
             es1 = C.eB[s1];
-            ids1 = C.idB[s1];
         }
         // pair map of entry k
-        ssa_pair_map(C, R, ps, es, bs, pt, et, w, G, dt, amp0);
+        ssa_pair_map(C, R, ps, es, bs, pt, et, g, dt, amp0);
         C.pB[t] = pt;
         C.eB[t] = et;
         if (t1 == t) {
             pt1 = pt;
             et1 = et;
         }
-        // Gaussian of entry k + 1
-        const T3<T> G1 = pair_gauss<T>(C.seed, step, (uint32_t)rep, ids1, idt1);
         if (sw) {
             ps.w = bs;
             C.pB[s] = ps;
@@ -996,11 +1029,10 @@ __global__ void __launch_bounds__(SSA_THREADS_MAX) k_ssa_colour(Ctx<T> C, const 
             ps = ps1;
             es = es1;
             bs = ps1.w;
-            ids = ids1;
             s = s1;
         }
-        t = t1; w = w1; pt = pt1; et = et1; G = G1;
-        r1 = r2; m1 = m2; n1 = n2; s1 = s2; t1 = t2; w1 = w2;
+        t = t1; g = g1; pt = pt1; et = et1;
+        r1 = r2; m1 = m2; n1 = n2; s1 = s2; t1 = t2; g1 = g2;
     }
     ps.w = bs;
     C.pB[s] = ps;

@@ -271,8 +271,8 @@ def test_ssa_launches_follow_colour_classes(box, bricks):
         return out
 
     ser, hyb, ssa = (S.step_launches(x) for x in ("SER", "HYBRID", "SSA"))
-    assert hyb - ser == classes(False)
-    assert ssa - (ser - 1) == classes(True)    # SSA: one copy-back in place of the two sweeps
+    assert hyb - ser == classes(False) + 1     # + the Gaussian pass
+    assert ssa - (ser - 1) == classes(True) + 1   # SSA: one copy-back in place of the two sweeps
     S.close()
 
 
