@@ -686,30 +686,102 @@ __global__ void __launch_bounds__(TILE_THREADS) k_force_tile(Ctx<T> C, const int
 // SER (Sec. III.B.1) over the neighbour list.
 // delta p_ij = -gamma_ij chi v_ij dt + sigma sqrt(chi) G_ij sqrt(dt),
 // gamma_ij = sigma^2/4 (beta_i + beta_j) (Eq. DPDE_fd), chi = w^2.
+//
+// Both sweeps are warp-cooperative: a warp takes 32 consecutive particles
+// (its lanes' own particles) and spreads all their list entries over its
+// lanes, one entry per lane per pass, so every lane evaluates a pair on every
+// pass however uneven the lists are. The pair values of one owner are summed
+// by a segmented shuffle scan (in entry order inside a pass, passes in order:
+// deterministic) and handed to the owner lane.
 // ---------------------------------------------------------------------------
+struct WarpEntries {
+    int lane, nn, incl, total;
+};
+
+__device__ __forceinline__ WarpEntries warp_entries(int nn) {
+    WarpEntries W;
+    W.lane = threadIdx.x & 31;
+    W.nn = nn;
+    int incl = nn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (W.lane >= o) incl += y;
+    }
+    W.incl = incl;
+    W.total = __shfl_sync(0xffffffffu, incl, 31);
+    return W;
+}
+
+// owner lane of flat entry f (the first lane whose inclusive prefix exceeds f)
+// and the entry's index k in the owner's list
+__device__ __forceinline__ void warp_entry_owner(const WarpEntries& W, int f, int& owner, int& k) {
+    int lo = 0;
+#pragma unroll
+    for (int st = 16; st > 0; st >>= 1) {
+        const int v = __shfl_sync(0xffffffffu, W.incl, lo + st - 1);
+        if (v <= f) lo += st;
+    }
+    owner = lo;
+    k = f - __shfl_sync(0xffffffffu, W.incl - W.nn, lo);
+}
+
+// segmented sum of v over lanes with equal owner; returns to every lane the
+// sum over this pass's entries of its own particle (0 if none)
+template <class T>
+__device__ __forceinline__ T warp_owner_sum(const WarpEntries& W, int f0, int owner, T v) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(0xffffffffu, v, o);
+        const int oy = __shfl_up_sync(0xffffffffu, owner, o);
+        if (W.lane >= o && oy == owner) v += y;
+    }
+    // my entries in this pass end at flat index incl - 1
+    const int last = W.incl - 1 - f0;
+    const bool mine = W.nn > 0 && last >= 0 && W.incl - W.nn < f0 + 32;
+    const T s = __shfl_sync(0xffffffffu, v, min(max(last, 0), 31));
+    return mine ? s : T(0);
+}
+
+// delta p_ij of list entry k of particle i (pair arithmetic of Eq. SER_p)
+template <class T>
+__device__ __forceinline__ T3<T> ser_dp(const Ctx<T>& C, int i, int k, uint32_t step, T dt, T sdt,
+                                        const vec_t<T>& pi, uint32_t idi, int rep) {
+    const int j = C.nbr_j[(size_t)k * C.N + i];
+    const T w = C.nbr_w[(size_t)k * C.N + i];
+    const vec_t<T> pj = C.pB[j];
+    const T3<T> G = pair_gauss<T>(C.seed, step, (uint32_t)rep, idi, C.idB[j]);
+    const T A = -(C.sig2_4 * (pi.w + pj.w)) * (w * w) * dt;
+    const T Bn = sdt * w;
+    return T3<T>{A * ((pi.x - pj.x) * C.inv_m) + Bn * G.x, A * ((pi.y - pj.y) * C.inv_m) + Bn * G.y,
+                 A * ((pi.z - pj.z) * C.inv_m) + Bn * G.z};
+}
+
 // first sweep: delta p_i = sum_j delta p_ij (Eq. SER_p)
 template <class T>
 __global__ void k_ser_sweep1(Ctx<T> C, T dt, T sqrt_dt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= C.N) return;
-    const int rep = C.rep_of_slot[i];
-    const vec_t<T> pi = C.pB[i];
-    const uint32_t idi = C.idB[i];
+    const int base = i - (int)(threadIdx.x & 31);
+    const WarpEntries W = warp_entries(i < C.N ? C.nbr_n[i] : 0);
     const uint32_t step = (uint32_t)*C.step;
-    const int nn = C.nbr_n[i];
     const T sdt = C.sigma * sqrt_dt;
     T ax = 0, ay = 0, az = 0;
-    for (int k = 0; k < nn; ++k) {
-        const int j = C.nbr_j[(size_t)k * C.N + i];
-        const T w = C.nbr_w[(size_t)k * C.N + i];
-        const vec_t<T> pj = C.pB[j];
-        const T3<T> G = pair_gauss<T>(C.seed, step, (uint32_t)rep, idi, C.idB[j]);
-        const T A = -(C.sig2_4 * (pi.w + pj.w)) * (w * w) * dt;
-        const T Bn = sdt * w;
-        ax += A * ((pi.x - pj.x) * C.inv_m) + Bn * G.x;
-        ay += A * ((pi.y - pj.y) * C.inv_m) + Bn * G.y;
-        az += A * ((pi.z - pj.z) * C.inv_m) + Bn * G.z;
+    for (int f0 = 0; f0 < W.total; f0 += 32) {
+        const int f = f0 + W.lane;
+        int o, k;
+        warp_entry_owner(W, f, o, k);
+        T3<T> d{0, 0, 0};
+        if (f < W.total) {
+            const int io = base + o;
+            d = ser_dp(C, io, k, step, dt, sdt, C.pB[io], C.idB[io], C.rep_of_slot[io]);
+        } else {
+            o = 32;
+        }
+        ax += warp_owner_sum(W, f0, o, d.x);
+        ay += warp_owner_sum(W, f0, o, d.y);
+        az += warp_owner_sum(W, f0, o, d.z);
     }
+    if (i >= C.N) return;
     vec_t<T> out;
     out.x = ax; out.y = ay; out.z = az; out.w = T(0);
     C.dp[i] = out;
@@ -725,33 +797,38 @@ __global__ void k_ser_sweep1(Ctx<T> C, T dt, T sqrt_dt) {
 template <class T>
 __global__ void k_ser_sweep2(Ctx<T> C, T dt, T sqrt_dt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= C.N) return;
-    const int rep = C.rep_of_slot[i];
-    const RepInfo& R = C.reps[rep];
-    const vec_t<T> pi = C.pB[i];
-    const vec_t<T> dpi = C.dp[i];
-    const uint32_t idi = C.idB[i];
+    const int base = i - (int)(threadIdx.x & 31);
+    const WarpEntries W = warp_entries(i < C.N ? C.nbr_n[i] : 0);
     const uint32_t step = (uint32_t)*C.step;
-    const int nn = C.nbr_n[i];
     const T sdt = C.sigma * sqrt_dt;
     const T hm = T(0.5) * C.inv_m;
-    const T vix = pi.x * C.inv_m, viy = pi.y * C.inv_m, viz = pi.z * C.inv_m;
     T tsum = 0;
-    for (int k = 0; k < nn; ++k) {
-        const int j = C.nbr_j[(size_t)k * C.N + i];
-        const T w = C.nbr_w[(size_t)k * C.N + i];
-        const vec_t<T> pj = C.pB[j];
-        const vec_t<T> dpj = C.dp[j];
-        const T3<T> G = pair_gauss<T>(C.seed, step, (uint32_t)rep, idi, C.idB[j]);
-        const T A = -(C.sig2_4 * (pi.w + pj.w)) * (w * w) * dt;
-        const T Bn = sdt * w;
-        const T vjx = pj.x * C.inv_m, vjy = pj.y * C.inv_m, vjz = pj.z * C.inv_m;
-        const T dx = A * (vix - vjx) + Bn * G.x;
-        const T dy = A * (viy - vjy) + Bn * G.y;
-        const T dz = A * (viz - vjz) + Bn * G.z;
-        tsum += dx * ((vix + vjx) + (dpi.x + dpj.x) * hm) + dy * ((viy + vjy) + (dpi.y + dpj.y) * hm) +
-                dz * ((viz + vjz) + (dpi.z + dpj.z) * hm);
+    for (int f0 = 0; f0 < W.total; f0 += 32) {
+        const int f = f0 + W.lane;
+        int o, k;
+        warp_entry_owner(W, f, o, k);
+        T tv = 0;
+        if (f < W.total) {
+            const int io = base + o;
+            const vec_t<T> pi = C.pB[io];
+            const vec_t<T> dpi = C.dp[io];
+            const int j = C.nbr_j[(size_t)k * C.N + io];
+            const T3<T> d = ser_dp(C, io, k, step, dt, sdt, pi, C.idB[io], C.rep_of_slot[io]);
+            const vec_t<T> pj = C.pB[j];
+            const vec_t<T> dpj = C.dp[j];
+            const T vix = pi.x * C.inv_m, viy = pi.y * C.inv_m, viz = pi.z * C.inv_m;
+            const T vjx = pj.x * C.inv_m, vjy = pj.y * C.inv_m, vjz = pj.z * C.inv_m;
+            tv = d.x * ((vix + vjx) + (dpi.x + dpj.x) * hm) + d.y * ((viy + vjy) + (dpi.y + dpj.y) * hm) +
+                 d.z * ((viz + vjz) + (dpi.z + dpj.z) * hm);
+        } else {
+            o = 32;
+        }
+        tsum += warp_owner_sum(W, f0, o, tv);
     }
+    if (i >= C.N) return;
+    const RepInfo& R = C.reps[C.rep_of_slot[i]];
+    const vec_t<T> pi = C.pB[i];
+    const vec_t<T> dpi = C.dp[i];
     vec_t<T> pn = pi;
     pn.x = pi.x + dpi.x; pn.y = pi.y + dpi.y; pn.z = pi.z + dpi.z;
     const T dK = ((pn.x - pi.x) * (pn.x + pi.x) + (pn.y - pi.y) * (pn.y + pi.y) +
