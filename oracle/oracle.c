@@ -665,3 +665,19 @@ int ora_observables(const ora_replica* rep, const ora_params* prm, const double*
     out[12] = (double)bad;
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Projection on the internal energies (Sec. IV.C): at the end of a step the */
+/* internal energies of the unconstrained update are all lowered by          */
+/* (E - E0) / N, E = U + K + sum eps of that update.                          */
+/* ------------------------------------------------------------------------ */
+int ora_project(const ora_replica* rep, const ora_params* prm, const double* q, const double* p,
+                double* eps, double E0)
+{
+    double out[13];
+    if (rep->n == 0) return 0;
+    if (ora_observables(rep, prm, q, p, eps, out) != 0) return -1;
+    double shift = (out[0] - E0) / (double)rep->n;
+    for (int64_t i = 0; i < rep->n; ++i) eps[i] -= shift;
+    return 0;
+}

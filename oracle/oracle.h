@@ -82,6 +82,11 @@ int ora_run(int32_t n_rep, const ora_replica* reps, const ora_params* prm,
 int ora_observables(const ora_replica* rep, const ora_params* prm, const double* q,
                     const double* p, const double* eps, double* out);
 
+/* Projection of Sec. IV.C on one replica, in place: eps_i -= (E - E0) / n,
+ * E the total energy (U + K + sum eps) of the given state. */
+int ora_project(const ora_replica* rep, const ora_params* prm, const double* q,
+                const double* p, double* eps, double E0);
+
 /* Cell grid of a replica as the library header defines it: ncell[3], k[3]. */
 int ora_cell_grid(const ora_replica* rep, double r_cut, int32_t* ncell, int32_t* k);
 

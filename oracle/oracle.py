@@ -73,6 +73,7 @@ def lib():
                               C.c_int64, C.c_int64, C.c_double, C.c_int32]
         L.ora_observables.argtypes = [C.POINTER(Replica), C.POINTER(Params), dp, dp, dp, dp]
         L.ora_cell_grid.argtypes = [C.POINTER(Replica), C.c_double, i32p, i32p]
+        L.ora_project.argtypes = [C.POINTER(Replica), C.POINTER(Params), dp, dp, dp, C.c_double]
         L.ora_ssa_order.argtypes = [C.POINTER(Replica), C.c_double, dp, C.c_int32, C.c_int64,
                                     i64p, i64p]
         L.ora_ssa_order.restype = C.c_int64
@@ -206,14 +207,38 @@ class System:
         self.q[s] = np.mod(self.q[s], box)
         self.q[s] = np.where(self.q[s] >= box, self.q[s] - box, self.q[s])
 
+    projection = None   # per-replica E0 when the projection of Sec. IV.C is on
+
+    def set_projection(self, E0=None, on=True):
+        """Turns the projection on (E0 per replica; default: the current
+        energies) or off."""
+        if not on:
+            self.projection = None
+        else:
+            self.projection = [self.observables(r)["E"] for r in range(self.R)] if E0 is None else list(E0)
+
     def run(self, nsteps: int, dt: float, scheme) -> None:
         scheme = SCHEMES.get(scheme, scheme)
-        rc = lib().ora_run(self.R, self.rep_arr, C.byref(self.prm), _ptr(self.q, C.c_double),
-                           _ptr(self.p, C.c_double), _ptr(self.eps, C.c_double),
-                           _ptr(self.F, C.c_double), self.step, nsteps, dt, scheme)
-        if rc:
-            raise ValueError("ora_run failed")
-        self.step += nsteps
+        per_call = 1 if self.projection is not None else nsteps
+        done = 0
+        while done < nsteps:
+            k = min(per_call, nsteps - done)
+            rc = lib().ora_run(self.R, self.rep_arr, C.byref(self.prm), _ptr(self.q, C.c_double),
+                               _ptr(self.p, C.c_double), _ptr(self.eps, C.c_double),
+                               _ptr(self.F, C.c_double), self.step, k, dt, scheme)
+            if rc:
+                raise ValueError("ora_run failed")
+            self.step += k
+            done += k
+            if self.projection is not None:
+                for r in range(self.R):
+                    s = slice(self.offsets[r], self.offsets[r + 1])
+                    q, p = np.ascontiguousarray(self.q[s]), np.ascontiguousarray(self.p[s])
+                    e = np.ascontiguousarray(self.eps[s])
+                    if lib().ora_project(C.byref(self.reps[r]), C.byref(self.prm), _ptr(q, C.c_double),
+                                         _ptr(p, C.c_double), _ptr(e, C.c_double), self.projection[r]):
+                        raise ValueError("ora_project failed")
+                    self.eps[s] = e
 
     def observables(self, r: int = 0) -> dict:
         s = slice(self.offsets[r], self.offsets[r + 1])

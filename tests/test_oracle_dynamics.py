@@ -115,3 +115,36 @@ def test_equilibrium_kinetic_equals_internal_temperature(ora, scheme, dt, tol):
         ti.append(o["Tint"])
     tk, ti = np.mean(tk), np.mean(ti)
     assert abs(tk / ti - 1) < tol, (tk, ti)
+
+
+# ---- projection on the internal energies (Sec. IV.C) ---------------------------
+
+def test_projection_holds_the_energy(ora):
+    """With the projection, E after every step equals E0 to rounding; without
+    it the same run drifts; and the projection lowers every eps_i by the same
+    amount (E - E0)/N."""
+    from paper_1507_06643_gb300 import inputs
+    w = inputs.plain_n1000("fp64")
+    spec = w.replicas[0]
+    q, p, e = inputs.workload_state(w)
+    rep = ora.make_replica(spec.n, spec.box, spec.cv, spec.bricks)
+    prm = ora.make_params(w.mass, w.r_cut, w.a, w.sigma, w.seed)
+    free = ora.System([rep], prm, q, p, e)
+    proj = ora.System([rep], prm, q, p, e)
+    proj.set_projection()
+    E0 = proj.projection[0]
+    drift_free = 0.0
+    for _ in range(15):
+        free.run(1, 0.02, "HYBRID")
+        before = proj.eps.copy()
+        pre = ora.System([rep], prm, proj.q, proj.p, proj.eps, step=proj.step)
+        pre.F[:] = proj.F
+        pre.run(1, 0.02, "HYBRID")
+        proj.run(1, 0.02, "HYBRID")
+        shift = pre.eps - proj.eps
+        assert np.allclose(shift, shift[0], rtol=0, atol=1e-12)
+        E_pre = pre.observables()["E"]
+        assert shift[0] == pytest.approx((E_pre - E0) / spec.n, rel=1e-9, abs=1e-15)
+        assert abs(proj.observables()["E"] - E0) < 1e-11 * abs(E0)
+        drift_free = max(drift_free, abs(free.observables()["E"] - E0) / abs(E0))
+    assert drift_free > 1e-9
