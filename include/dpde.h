@@ -320,6 +320,19 @@ const char* dpde_noalloc_last_error(void);
 int dpde_step_profiled(dpde_handle* h, int64_t n, double dt, int32_t scheme,
                        double* phase_ms);
 
+/* ---- projection (Sec. IV.C) ---- */
+
+/* Projection on the internal energies: with enable = 1, every later step
+ * ends by lowering each eps_i of replica r by (E_r - E0[r]) / n_r, where E_r
+ * is the total energy (U + K + sum eps) of the step's unconstrained update,
+ * so that the total energy stays at E0[r]. E0: host array of n_replicas
+ * doubles, or NULL for the handle's current energies (as dpde_observables
+ * reports them). enable = 0 turns it off. Waits for the handle's stream and
+ * drops the captured step graphs. The setting is not part of a checkpoint.
+ * A step whose projection makes some eps_i <= 0 reports DPDE_ERR_NEG_EPS like
+ * any other step. */
+int dpde_set_projection(dpde_handle* h, int32_t enable, const double* E0);
+
 /* ---- tuning ---- */
 
 /* Launch parameters of a handle. None of them changes what is computed; the

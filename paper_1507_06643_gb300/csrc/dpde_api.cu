@@ -46,6 +46,10 @@ struct dpde_handle {
     cudaStream_t cap_stream = nullptr;
     // device buffers
     void *qA = nullptr, *pA = nullptr, *qB = nullptr, *pB = nullptr, *F = nullptr, *dp = nullptr;
+    void* upot = nullptr;            // per-particle potential energy share (T)
+    // projection on the internal energies (Sec. IV.C)
+    bool project = false;
+    double *proj_e0 = nullptr, *proj_shift = nullptr, *proj_partial = nullptr;
     void *eA = nullptr, *eB = nullptr, *nbr_w = nullptr, *fwd_w = nullptr, *fwd_g = nullptr;
     int *cA = nullptr, *cB = nullptr, *nbr_j = nullptr, *nbr_n = nullptr, *fwd_j = nullptr, *fwd_n = nullptr;
     int4 *tile_org = nullptr, *tile_dim = nullptr;
@@ -108,6 +112,7 @@ Ctx<T> make_ctx(dpde_handle* h) {
     C.qB = (vec*)h->qB; C.pB = (vec*)h->pB; C.eB = (E*)h->eB; C.cB = h->cB;
     C.idB = h->idB;
     C.F = (vec*)h->F; C.dp = (vec*)h->dp;
+    C.upot = (T*)h->upot;
     C.key = h->key; C.tmp = h->tmp;
     C.count = h->cnt; C.fill = h->cnt + h->ncells; C.start = h->start;
     C.nbr_j = h->nbr_j; C.nbr_w = (T*)h->nbr_w; C.nbr_n = h->nbr_n; C.nbr_cap = h->nbr_cap;
@@ -202,6 +207,15 @@ void enqueue_step(dpde_handle* h, cudaStream_t st, double dt_d, int scheme) {
     else if (scheme == DPDE_SEM) k_sem<T><<<nb, h->block, 0, st>>>(C, dt, sqrt_dt);
     else k_copy_back<T><<<nb, h->block, 0, st>>>(C);
     phase(h, st, DPDE_PHASE_SWEEP2, 1);
+    if (h->project) {
+        phase(h, st, DPDE_PHASE_OTHER, 0);
+        if (h->nchunks > 0)
+            k_proj_chunks<T><<<h->nchunks, OBS_THREADS, 0, st>>>(C, h->chunk_begin, h->chunk_end, h->proj_partial);
+        k_proj_reps<T><<<ceil_div(h->R, 128), 128, 0, st>>>(C, h->proj_partial, h->rep_chunk_begin, h->R,
+                                                             h->proj_e0, h->proj_shift);
+        k_proj_apply<T><<<nb, h->block, 0, st>>>(C, h->proj_shift);
+        phase(h, st, DPDE_PHASE_OTHER, 1);
+    }
     k_step_inc<<<1, 1, 0, st>>>(h->d_step);
 }
 
@@ -260,7 +274,7 @@ void free_all(dpde_handle* h) {
             if (ev) cudaEventDestroy(ev);
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
-    void* bufs[] = {h->qA, h->pA, h->qB, h->pB, h->F, h->dp, h->eA, h->eB, h->nbr_w, h->cA, h->cB, h->nbr_j,
+    void* bufs[] = {h->qA, h->pA, h->qB, h->pB, h->F, h->dp, h->upot, h->proj_e0, h->proj_shift, h->proj_partial, h->eA, h->eB, h->nbr_w, h->cA, h->cB, h->nbr_j,
                     h->nbr_n, h->fwd_j, h->fwd_w, h->fwd_g, h->fwd_n, h->tile_org, h->tile_dim, h->col_cells[0], h->col_cells[1], h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
                     h->rep_of_cell, h->brick_rep, h->tab, h->chunk_rep, h->chunk_begin, h->chunk_end,
                     h->rep_chunk_begin, h->partial, h->obs_out, h->d_reps, h->d_step, h->d_status,
@@ -480,6 +494,10 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     CKC(cudaMalloc(&h->pB, vsz * n1));
     CKC(cudaMalloc(&h->F, vsz * n1));
     CKC(cudaMalloc(&h->dp, vsz * n1));
+    CKC(cudaMalloc(&h->upot, tsz * n1));
+    CKC(cudaMalloc(&h->proj_e0, sizeof(double) * (size_t)h->R));
+    CKC(cudaMalloc(&h->proj_shift, sizeof(double) * (size_t)h->R));
+    CKC(cudaMalloc(&h->proj_partial, sizeof(double) * std::max<size_t>(1, chunk_rep.size())));
     CKC(cudaMalloc(&h->eA, esz * n1));
     CKC(cudaMalloc(&h->eB, esz * n1));
     CKC(cudaMalloc(&h->cA, sizeof(int) * n1));
@@ -652,6 +670,32 @@ int dpde_step(dpde_handle* h, int64_t n, double dt, int32_t scheme, int32_t use_
         CK(h, cudaGetLastError());
     }
     h->step += n;
+    return DPDE_OK;
+}
+
+int dpde_set_projection(dpde_handle* h, int32_t enable, const double* E0) {
+    if (!h || (enable != 0 && enable != 1)) return DPDE_ERR_ARG;
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    if (!enable) {
+        h->project = false;
+        return DPDE_OK;
+    }
+    std::vector<double> e0((size_t)h->R);
+    if (E0) {
+        for (int r = 0; r < h->R; ++r) {
+            if (!std::isfinite(E0[r])) return fail(h, DPDE_ERR_ARG, "E0 must be finite");
+            e0[r] = E0[r];
+        }
+    } else {
+        std::vector<dpde_obs> obs((size_t)h->R);
+        const int rc = dpde_observables(h, obs.data());
+        if (rc != DPDE_OK && rc != DPDE_ERR_NEG_EPS) return rc;
+        for (int r = 0; r < h->R; ++r) e0[r] = obs[r].E;
+    }
+    CK(h, cudaMemcpy(h->proj_e0, e0.data(), sizeof(double) * (size_t)h->R, cudaMemcpyHostToDevice));
+    h->project = true;
     return DPDE_OK;
 }
 

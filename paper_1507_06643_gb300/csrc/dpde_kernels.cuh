@@ -20,6 +20,7 @@ template <class T> struct Ctx {
     vec* qB; vec* pB; E* eB; int* cB;
     uint32_t* idB;   // compact id copy of set B (for neighbour gathers)
     vec* F; vec* dp;
+    T* upot;         // per particle: its share of U at the step's positions, 1/2 sum_j v(r_ij)
     int* key;        // global cell of each slot (A order), written by the drift
     int* tmp;        // slots binned by cell, arbitrary order inside a cell
     int* count;      // per-cell counts (ncells), followed by fill (ncells)
@@ -386,6 +387,7 @@ template <> __device__ __forceinline__ double trsqrt(double x) { return rsqrt(x)
 template <class T>
 struct PairOut {
     T fx = 0, fy = 0, fz = 0;
+    T w2 = 0;   // sum of w^2 over the neighbours (potential energy)
     int nn = 0, nf = 0;
 };
 
@@ -403,6 +405,7 @@ __device__ __forceinline__ void force_hit(const Ctx<T>& C, int i, int j, bool fw
         const T f = C.a * w * ir;
         o.fx += f * dx; o.fy += f * dy; o.fz += f * dz;
     }
+    o.w2 += w * w;
     if (LM == LIST_ALL || (LM == LIST_CROSS && cross)) {
         if (o.nn < C.nbr_cap) {
             C.nbr_j[(size_t)o.nn * N + i] = j;
@@ -431,6 +434,8 @@ __device__ __forceinline__ void force_finish(const Ctx<T>& C, int i, T half_dt, 
     vec_t<T> f;
     f.x = o.fx; f.y = o.fy; f.z = o.fz; f.w = T(0);
     C.F[i] = f;
+    // v(r) = (a r_c / 2) w^2 per pair, each pair seen from both sides
+    C.upot[i] = T(0.25) * C.a * C.rc * o.w2;
     if (kick) {
         vec_t<T> pv = C.pB[i];
         pv.x += half_dt * o.fx; pv.y += half_dt * o.fy; pv.z += half_dt * o.fz;
@@ -1126,13 +1131,65 @@ __global__ void k_refresh_beta(Ctx<T> C) {
 __global__ void k_step_inc(long long* step) { *step += 1; }
 
 // ---------------------------------------------------------------------------
+// Projection on the internal energies (Sec. IV.C): after the step, every
+// eps_i of a replica is lowered by (E - E0)/N, E = U + K + sum eps of the
+// unconstrained update (set A after the FD part; U from the force pass at the
+// same positions). Per-chunk sums in a fixed order, then per replica.
+// ---------------------------------------------------------------------------
+constexpr int OBS_THREADS = 256;
+
+template <class T>
+__global__ void k_proj_chunks(Ctx<T> C, const int* __restrict__ chunk_begin, const int* __restrict__ chunk_end,
+                              double* __restrict__ partial) {
+    const int ch = blockIdx.x;
+    double acc = 0.0;
+    const double hm = 0.5 / (double)C.m;
+    for (int i = chunk_begin[ch] + threadIdx.x; i < chunk_end[ch]; i += blockDim.x) {
+        const vec_t<T> p = C.pA[i];
+        acc += ((double)p.x * p.x + (double)p.y * p.y + (double)p.z * p.z) * hm + (double)C.upot[i] +
+               eps_value(C.eA[i]);
+    }
+    __shared__ double sh[OBS_THREADS];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = OBS_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[ch] = sh[0];
+}
+
+template <class T>
+__global__ void k_proj_reps(Ctx<T> C, const double* __restrict__ partial, const int* __restrict__ rep_chunk_begin,
+                            int R, const double* __restrict__ E0, double* __restrict__ shift) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    double E = 0.0;
+    for (int ch = rep_chunk_begin[r]; ch < rep_chunk_begin[r + 1]; ++ch) E += partial[ch];
+    const int n = C.reps[r].n;
+    shift[r] = n > 0 ? (E - E0[r]) / (double)n : 0.0;
+}
+
+template <class T>
+__global__ void k_proj_apply(Ctx<T> C, const double* __restrict__ shift) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C.N) return;
+    const int r = C.rep_of_slot[i];
+    const eps_t<T> e = eps_add(C.eA[i], (T)(-shift[r]));
+    C.eA[i] = e;
+    vec_t<T> p = C.pA[i];
+    p.w = beta_of(e, C.reps[r]);
+    C.pA[i] = p;
+    check_state<T>(C.status, p, e);
+}
+
+// ---------------------------------------------------------------------------
 // observables: per-chunk sums (a chunk lies inside one replica), then per
 // replica sums of the chunks in order -- deterministic.
 // terms: 0 K, 1 U, 2 Eint, 3-5 P, 6 sum C_v/eps, 7 |F|^2, 8 Laplacian U,
 //        9 neg eps, 10 nonfinite
 // ---------------------------------------------------------------------------
 constexpr int NTERMS = 11;
-constexpr int OBS_THREADS = 256;
 
 template <class T>
 __global__ void k_obs_chunks(Ctx<T> C, const int* __restrict__ chunk_rep, const int* __restrict__ chunk_begin,

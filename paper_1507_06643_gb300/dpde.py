@@ -73,7 +73,8 @@ EXPORTS = ["dpde_create", "dpde_set_state", "dpde_get_state", "dpde_step", "dpde
            "dpde_observables", "dpde_get_step", "dpde_destroy", "dpde_last_error",
            "dpde_debug_philox", "dpde_debug_gaussian", "dpde_step_profiled", "dpde_get_cells",
            "dpde_checkpoint", "dpde_restore", "dpde_observables_noalloc", "dpde_noalloc_last_error",
-           "dpde_step_launches", "dpde_get_tuning", "dpde_set_tuning", "dpde_autotune"]
+           "dpde_step_launches", "dpde_get_tuning", "dpde_set_tuning", "dpde_autotune",
+           "dpde_set_projection"]
 PHASES = ["kick_drift", "scan", "gather", "force", "ssa", "sweep1", "sweep2", "other"]
 
 
@@ -107,6 +108,7 @@ def lib():
         L.dpde_get_cells.argtypes = [vp, C.POINTER(C.c_int32)]
         L.dpde_step_launches.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64)]
         L.dpde_get_tuning.argtypes = [vp, C.POINTER(dpde_tuning)]
+        L.dpde_set_projection.argtypes = [vp, C.c_int32, C.POINTER(C.c_double)]
         L.dpde_set_tuning.argtypes = [vp, C.POINTER(dpde_tuning)]
         L.dpde_autotune.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, C.POINTER(dpde_tuning)]
         L.dpde_step_profiled.argtypes = [vp, C.c_int64, C.c_double, C.c_int32, dp]
@@ -174,6 +176,16 @@ def dpde_get_step(h) -> int:
     out = C.c_int64(0)
     _check(h, lib().dpde_get_step(h, C.byref(out)))
     return int(out.value)
+
+
+def dpde_set_projection(h, enable=True, E0=None):
+    """Projection on the internal energies (Sec. IV.C); E0 per replica, or
+    None for the current energies."""
+    arr = None
+    if E0 is not None:
+        arr = np.ascontiguousarray(np.asarray(E0, dtype=np.float64).ravel())
+    _check(h, lib().dpde_set_projection(h, 1 if enable else 0,
+                                        arr.ctypes.data_as(C.POINTER(C.c_double)) if arr is not None else None))
 
 
 def dpde_get_tuning(h) -> dict:
@@ -309,6 +321,9 @@ class System:
 
     def step_launches(self, scheme) -> int:
         return dpde_step_launches(self.h, scheme)
+
+    def set_projection(self, enable=True, E0=None):
+        dpde_set_projection(self.h, enable, E0)
 
     def tuning(self) -> dict:
         return dpde_get_tuning(self.h)

@@ -276,6 +276,61 @@ def test_ssa_launches_follow_colour_classes(box, bricks):
     S.close()
 
 
+# ---- projection on the internal energies (Sec. IV.C) ----------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("scheme", ["HYBRID", "SER"])
+def test_parity_with_projection(precision, scheme):
+    """Projected steps against the projected oracle, both from the oracle's E0."""
+    from oracle import oracle as O
+    from paper_1507_06643_gb300 import dpde
+    from gpu_util import oracle_cells
+    specs = [(1000, (cube(1000),) * 3, 100.0, 1.0, (2, 2, 2))]
+    compared = 0
+    for seed in range(41, 49):
+        q, p, e = make_state(specs, seed, precision == "mixed")
+        S = dpde.System(dpde.make_params(1.0, 1.0, 25.0, 3.0, 42, precision),
+                        [dpde.make_replica(1000, specs[0][1], 100.0, (2, 2, 2))])
+        S.set_state(q, p, e)
+        ref = O.System([O.make_replica(1000, specs[0][1], 100.0, (2, 2, 2))], O.make_params(1.0, 1.0, 25.0, 3.0, 42),
+                       q, p, e)
+        ref.set_projection()
+        S.set_projection(True, ref.projection)
+        flips = False
+        for _ in range(8):
+            S.step(1, 0.01, scheme)
+            ref.run(1, 0.01, scheme)
+            flips |= bool(np.any(S.get_cells() != oracle_cells(ref.q, specs, ref.offsets)))
+        qg, pg, eg = S.get_state()
+        S.close()
+        if flips and scheme == "HYBRID":
+            continue
+        tol = TOL[precision]
+        assert rel_err(pg, ref.p) < tol and rel_err(eg, ref.eps) < tol, seed
+        compared += 1
+        if compared == 2:
+            break
+    assert compared >= 1
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 2e-7)])
+def test_projection_holds_the_energy(precision, tol):
+    from paper_1507_06643_gb300 import dpde
+    specs = [(20000, (cube(20000),) * 3, 50.0, 1.0, (3, 3, 3))]
+    q, p, e = make_state(specs, 12, precision == "mixed")
+    S = dpde.System(dpde.make_params(precision=precision), [dpde.make_replica(*specs[0][:3], (3, 3, 3))])
+    S.set_state(q, p, e)
+    S.step(20, 0.01, "HYBRID")
+    E0 = S.observables()[0]["E"]
+    S.set_projection()
+    S.step(50, 0.01, "HYBRID")
+    assert abs(S.observables()[0]["E"] - E0) < tol * abs(E0)
+    S.set_projection(False)
+    S.step(50, 0.01, "HYBRID")
+    assert abs(S.observables()[0]["E"] - E0) > tol * abs(E0)
+    S.close()
+
+
 # ---- tuning -------------------------------------------------------------------------
 
 def _run_tuned(precision, tuning, steps=5, scheme="HYBRID"):
