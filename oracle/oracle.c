@@ -229,6 +229,33 @@ static int64_t all_pairs(const ora_replica* rep, double r_cut, const double* q, 
 
 /* F_i = -grad_{q_i} U with v(r) = (a r_cut/2)(1 - r/r_cut)^2, so the pair
  * force on i is a (1 - r/r_cut) (q_i - q_j)/r, and -(it) on j. */
+/* Eq. (Ep): v = 4 eps_LJ((r_LJ/r)^12 - (r_LJ/r)^6) - eps_sh - f_sp (r - r_cut)
+ * below r_cut, with eps_sh and f_sp fixed by v(r_cut) = 0 and v'(r_cut) = 0,
+ * i.e. eps_sh = v_LJ(r_cut), f_sp = v_LJ'(r_cut). Soft repulsion otherwise. */
+static void lj_terms(double eps, double rlj, double r, double* v, double* dv, double* d2v)
+{
+    double s6 = pow(rlj / r, 6.0), s12 = s6 * s6;
+    *v = 4.0 * eps * (s12 - s6);
+    *dv = 4.0 * eps * (-12.0 * s12 + 6.0 * s6) / r;
+    *d2v = 4.0 * eps * (156.0 * s12 - 42.0 * s6) / (r * r);
+}
+
+void ora_pair_potential(const ora_params* prm, double r, double* v, double* dv, double* d2v)
+{
+    if (prm->potential == ORA_POT_LJ) {
+        double vc, dvc, d2vc;
+        lj_terms(prm->lj_eps, prm->lj_r, prm->r_cut, &vc, &dvc, &d2vc);
+        lj_terms(prm->lj_eps, prm->lj_r, r, v, dv, d2v);
+        *v -= vc + dvc * (r - prm->r_cut);
+        *dv -= dvc;
+        return;
+    }
+    double w = 1.0 - r / prm->r_cut;
+    *v = 0.5 * prm->a * prm->r_cut * w * w;
+    *dv = -prm->a * w;
+    *d2v = prm->a / prm->r_cut;
+}
+
 int ora_forces(const ora_replica* rep, const ora_params* prm, const double* q, double* F)
 {
     int64_t *pi, *pj;
@@ -241,7 +268,9 @@ int ora_forces(const ora_replica* rep, const ora_params* prm, const double* q, d
         double r2 = min_image(rep, q, i, j, dx);
         double r = sqrt(r2);
         if (r == 0.0) continue;
-        double f = prm->a * (1.0 - r / prm->r_cut) / r;
+        double v, dv, d2v;
+        ora_pair_potential(prm, r, &v, &dv, &d2v);
+        double f = -dv / r;   /* F_i = -v'(r) (q_i - q_j)/r */
         for (int d = 0; d < 3; ++d) {
             F[3 * i + d] += f * dx[d];
             F[3 * j + d] -= f * dx[d];
@@ -634,14 +663,13 @@ int ora_observables(const ora_replica* rep, const ora_params* prm, const double*
         int64_t np = all_pairs(rep, prm->r_cut, q, &pi, &pj);
         if (np < 0) return -1;
         double dx[3];
-        double a = prm->a, rc = prm->r_cut;
         for (int64_t t = 0; t < np; ++t) {
             double r = sqrt(min_image(rep, q, pi[t], pj[t], dx));
-            double w = 1.0 - r / rc;
-            U += 0.5 * a * rc * w * w;
-            /* v'' + (d-1) v'/r for v = (a rc/2) w^2: v' = -a w, v'' = a / rc;
-             * counted once for i and once for j */
-            if (r > 0.0) lap += 2.0 * (a / rc - 2.0 * a * w / r);
+            double v, dv, d2v;
+            ora_pair_potential(prm, r, &v, &dv, &d2v);
+            U += v;
+            /* Laplacian of U: v'' + (d-1) v'/r, counted once for i and once for j */
+            if (r > 0.0) lap += 2.0 * (d2v + 2.0 * dv / r);
         }
         free(pi);
         free(pj);

@@ -29,8 +29,16 @@ typedef struct ora_params {
     double   mass, r_cut, a, sigma;
     uint64_t seed;
     int32_t  noise;     /* 1: Philox Gaussians; 0: G = 0 (tests only) */
-    int32_t  reserved;
+    int32_t  potential; /* ORA_POT_SOFT or ORA_POT_LJ */
+    double   lj_eps, lj_r;   /* Lennard-Jones eps_LJ and r_LJ (ORA_POT_LJ) */
 } ora_params;
+
+/* Pair potentials: the soft repulsion v = (a r_cut / 2)(1 - r/r_cut)^2, or the
+ * shifted, splined and truncated Lennard-Jones potential of Eq. (Ep). */
+enum { ORA_POT_SOFT = 0, ORA_POT_LJ = 1 };
+
+/* v(r), v'(r), v''(r) of the pair potential (r < r_cut). */
+void ora_pair_potential(const ora_params* prm, double r, double* v, double* dv, double* d2v);
 
 typedef struct ora_replica {
     int64_t n;

@@ -40,7 +40,10 @@ def build(force: bool = False) -> str:
 class Params(C.Structure):
     _fields_ = [("mass", C.c_double), ("r_cut", C.c_double), ("a", C.c_double),
                 ("sigma", C.c_double), ("seed", C.c_uint64), ("noise", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("potential", C.c_int32), ("lj_eps", C.c_double), ("lj_r", C.c_double)]
+
+
+POT_SOFT, POT_LJ = 0, 1
 
 
 class Replica(C.Structure):
@@ -74,6 +77,7 @@ def lib():
         L.ora_observables.argtypes = [C.POINTER(Replica), C.POINTER(Params), dp, dp, dp, dp]
         L.ora_cell_grid.argtypes = [C.POINTER(Replica), C.c_double, i32p, i32p]
         L.ora_project.argtypes = [C.POINTER(Replica), C.POINTER(Params), dp, dp, dp, C.c_double]
+        L.ora_pair_potential.argtypes = [C.POINTER(Params), C.c_double, dp, dp, dp]
         L.ora_ssa_order.argtypes = [C.POINTER(Replica), C.c_double, dp, C.c_int32, C.c_int64,
                                     i64p, i64p]
         L.ora_ssa_order.restype = C.c_int64
@@ -89,8 +93,16 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def make_params(mass=1.0, r_cut=1.0, a=25.0, sigma=3.0, seed=0, noise=True) -> Params:
-    return Params(mass, r_cut, a, sigma, seed, 1 if noise else 0, 0)
+def make_params(mass=1.0, r_cut=1.0, a=25.0, sigma=3.0, seed=0, noise=True, potential=POT_SOFT,
+                lj_eps=1.0, lj_r=1.0) -> Params:
+    return Params(mass, r_cut, a, sigma, seed, 1 if noise else 0, potential, lj_eps, lj_r)
+
+
+def pair_potential(prm: Params, r: float):
+    """(v, v', v'') of the pair potential at r."""
+    v, dv, d2v = C.c_double(), C.c_double(), C.c_double()
+    lib().ora_pair_potential(C.byref(prm), float(r), C.byref(v), C.byref(dv), C.byref(d2v))
+    return v.value, dv.value, d2v.value
 
 
 def make_replica(n, box, cv, bricks=(1, 1, 1)) -> Replica:

@@ -145,6 +145,26 @@ def batched_256(precision: str = "mixed", n_replicas: int = 256, seed: int = 100
     return Workload("batched_256", reps, steps=1000, seed=seed, precision=precision)
 
 
+def fcc_state(cells: int, density: float, kT: float, cv: float, mass: float, seed: int,
+              jitter: float = 0.02):
+    """Face-centred cubic crystal of cells^3 unit cells (4 sites each) at the
+    given number density, sites displaced by N(0, jitter^2) per component,
+    Maxwellian momenta at kT with the mean removed, eps = cv kT (1 +- 5%).
+    Returns (q, p, eps, L)."""
+    rng = np.random.default_rng(seed)
+    a = (4.0 / density) ** (1.0 / 3.0)
+    base = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    grid = np.stack(np.meshgrid(np.arange(cells), np.arange(cells), np.arange(cells), indexing="ij"), -1)
+    q = ((grid.reshape(-1, 1, 3) + base.reshape(1, 4, 3)).reshape(-1, 3) + 0.25) * a
+    L = cells * a
+    q = np.mod(q + rng.normal(0.0, jitter, q.shape), L)
+    n = len(q)
+    p = rng.standard_normal((n, 3)) * math.sqrt(mass * kT)
+    p -= p.mean(axis=0)
+    e = cv * kT * (1 + 0.05 * rng.uniform(-1, 1, n))
+    return q, p, e, L
+
+
 WORKLOADS = {
     "plain_n1000": plain_n1000,
     "equilibrium_n108000": equilibrium_n108000,
