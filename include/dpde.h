@@ -156,14 +156,25 @@ extern "C" {
 #define DPDE_SSA     3
 
 /* Global model parameters (shared by all replicas of a handle). */
+/* Pair potentials. DPDE_POT_SOFT: v = (a r_cut / 2)(1 - r/r_cut)^2.
+ * DPDE_POT_LJ: the shifted, splined and truncated Lennard-Jones potential of
+ * Eq. (Ep), v = 4 eps_LJ((r_LJ/r)^12 - (r_LJ/r)^6) - eps_sh - f_sp (r - r_cut)
+ * below r_cut with eps_sh, f_sp fixed by v(r_cut) = v'(r_cut) = 0; r_cut is
+ * the same cutoff as chi's (the paper writes both with r_cut). Coincident
+ * particles (r = 0) exert no force; their LJ energy term is left out. */
+#define DPDE_POT_SOFT 0
+#define DPDE_POT_LJ   1
+
 typedef struct dpde_params {
     double   mass;       /* m  > 0                                          */
-    double   r_cut;      /* r_cut > 0: range of chi and of the soft force   */
+    double   r_cut;      /* r_cut > 0: range of chi and of the potential    */
     double   a;          /* soft-repulsion amplitude a >= 0                 */
     double   sigma;      /* fluctuation strength sigma >= 0, Eq. (DPDE_fd)  */
     uint64_t seed;       /* Philox key                                      */
     int32_t  precision;  /* DPDE_FP64 or DPDE_MIXED                         */
-    int32_t  reserved;   /* must be 0                                       */
+    int32_t  potential;  /* DPDE_POT_SOFT (0) or DPDE_POT_LJ                */
+    double   lj_eps;     /* eps_LJ >= 0 (DPDE_POT_LJ)                       */
+    double   lj_r;       /* r_LJ > 0 (DPDE_POT_LJ)                          */
 } dpde_params;
 
 /* One independent system ("replica", one of the N_traj trajectories of

@@ -125,6 +125,7 @@ Ctx<T> make_ctx(dpde_handle* h) {
     C.rc = (T)h->prm.r_cut; C.rc2 = (T)(h->prm.r_cut * h->prm.r_cut);
     C.inv_rc = (T)(1.0 / h->prm.r_cut);
     C.a = (T)h->prm.a; C.sigma = (T)h->prm.sigma;
+    C.pot = cast_pot<T>(make_pot(h->prm.potential, h->prm.a, h->prm.r_cut, h->prm.lj_eps, h->prm.lj_r));
     C.sig2_4 = (T)(h->prm.sigma * h->prm.sigma / 4.0);
     C.seed = make_uint2((uint32_t)(h->prm.seed & 0xffffffffu), (uint32_t)(h->prm.seed >> 32));
     return C;
@@ -347,7 +348,10 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     *out = nullptr;
     if (!params || !replicas || n_replicas < 1) return fail(nullptr, DPDE_ERR_ARG, "bad params/replicas");
     const dpde_params& P = *params;
-    if (!(P.mass > 0) || !(P.r_cut > 0) || !(P.a >= 0) || !(P.sigma >= 0) || P.reserved != 0 ||
+    if (!(P.mass > 0) || !(P.r_cut > 0) || !(P.a >= 0) || !(P.sigma >= 0) ||
+        (P.potential != DPDE_POT_SOFT && P.potential != DPDE_POT_LJ) ||
+        (P.potential == DPDE_POT_LJ && (!(P.lj_eps >= 0) || !(P.lj_r > 0) || !std::isfinite(P.lj_eps) ||
+                                        !std::isfinite(P.lj_r))) ||
         (P.precision != DPDE_FP64 && P.precision != DPDE_MIXED))
         return fail(nullptr, DPDE_ERR_ARG, "invalid dpde_params");
     dpde_handle* h = new dpde_handle();

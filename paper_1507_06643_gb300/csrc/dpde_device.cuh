@@ -17,6 +17,8 @@
 // c + d is (o_i - o_j) - d * l, which also gives the periodic image.
 #pragma once
 
+#include <cmath>
+
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -177,6 +179,64 @@ __device__ __forceinline__ T3<T> pair_gauss(uint2 key, uint32_t step, uint32_t r
     }
     return g;
 }
+
+// ---------------------------------------------------------------------------
+// Pair potential: the soft repulsion v = (a r_c/2)(1 - r/r_c)^2, or the
+// shifted, splined, truncated Lennard-Jones potential of Eq. (Ep),
+// v = 4 eps((r_LJ/r)^12 - (r_LJ/r)^6) - eps_sh - f_sp (r - r_c) with eps_sh =
+// v_LJ(r_c), f_sp = v_LJ'(r_c) so that v(r_c) = v'(r_c) = 0.
+// ---------------------------------------------------------------------------
+template <class T> struct PotT {
+    int kind;                       // DPDE_POT_SOFT or DPDE_POT_LJ
+    T a, rc, inv_rc, half_arc;      // soft: a, r_c, 1/r_c, a r_c / 2
+    T lj4e, ljr2, ljesh, ljfsp;     // LJ: 4 eps, r_LJ^2, eps_sh, f_sp
+};
+
+// For 0 < r2 < r_c^2 and ir = 1/sqrt(r2): v(r), fr = -v'(r)/r (so that the
+// force on i is fr (q_i - q_j)) and lap = v''(r) + 2 v'(r)/r.
+template <class T>
+__device__ __forceinline__ void pair_pot(const PotT<T>& P, T r2, T ir, T& v, T& fr, T& lap) {
+    const T r = r2 * ir;
+    if (P.kind == 1) {
+        const T ir2 = ir * ir;
+        const T s2 = P.ljr2 * ir2, s6 = s2 * s2 * s2, s12 = s6 * s6;
+        const T dv = P.lj4e * (T(6) * s6 - T(12) * s12) * ir - P.ljfsp;
+        v = P.lj4e * (s12 - s6) - P.ljesh - P.ljfsp * (r - P.rc);
+        fr = -dv * ir;
+        lap = P.lj4e * (T(156) * s12 - T(42) * s6) * ir2 + T(2) * dv * ir;
+    } else {
+        const T w = T(1) - r * P.inv_rc;
+        v = P.half_arc * w * w;
+        fr = P.a * w * ir;
+        lap = P.a * P.inv_rc - T(2) * P.a * w * ir;
+    }
+}
+
+// Constants of the pair potential from the parameters (host side, double).
+inline PotT<double> make_pot(int kind, double a, double rc, double lj_eps, double lj_r) {
+    PotT<double> P{};
+    P.kind = kind;
+    P.a = a;
+    P.rc = rc;
+    P.inv_rc = 1.0 / rc;
+    P.half_arc = 0.5 * a * rc;
+    if (kind == 1) {
+        const double s6 = std::pow(lj_r / rc, 6.0), s12 = s6 * s6;
+        P.lj4e = 4.0 * lj_eps;
+        P.ljr2 = lj_r * lj_r;
+        P.ljesh = 4.0 * lj_eps * (s12 - s6);                  // v_LJ(r_c)
+        P.ljfsp = 4.0 * lj_eps * (6.0 * s6 - 12.0 * s12) / rc;  // v_LJ'(r_c)
+    }
+    return P;
+}
+
+template <class T> inline PotT<T> cast_pot(const PotT<double>& P) {
+    return PotT<T>{P.kind, (T)P.a, (T)P.rc, (T)P.inv_rc, (T)P.half_arc, (T)P.lj4e, (T)P.ljr2, (T)P.ljesh, (T)P.ljfsp};
+}
+
+// v at r = 0: the soft potential's maximum; no LJ term
+template <class T>
+__device__ __forceinline__ T pair_pot_at_zero(const PotT<T>& P) { return P.kind == 1 ? T(0) : P.half_arc; }
 
 // Status bits raised by the kernels (read and cleared by the host).
 enum : unsigned int { ST_NEG_EPS = 1u, ST_NONFINITE = 2u, ST_CAPACITY = 4u };

@@ -44,6 +44,7 @@ template <class T> struct Ctx {
     unsigned int* status;
     int N, ncells;
     T m, inv_m, rc, rc2, inv_rc, a, sigma, sig2_4;
+    PotT<T> pot;
     uint2 seed;
 };
 
@@ -387,7 +388,7 @@ template <> __device__ __forceinline__ double trsqrt(double x) { return rsqrt(x)
 template <class T>
 struct PairOut {
     T fx = 0, fy = 0, fz = 0;
-    T w2 = 0;   // sum of w^2 over the neighbours (potential energy)
+    T u = 0;    // sum of v(r) over the neighbours
     int nn = 0, nf = 0;
 };
 
@@ -402,10 +403,13 @@ __device__ __forceinline__ void force_hit(const Ctx<T>& C, int i, int j, bool fw
     if (r2 > T(0)) {
         const T ir = trsqrt(r2);
         w = T(1) - r2 * ir * C.inv_rc;
-        const T f = C.a * w * ir;
-        o.fx += f * dx; o.fy += f * dy; o.fz += f * dz;
+        T v, fr, lap;
+        pair_pot(C.pot, r2, ir, v, fr, lap);
+        o.fx += fr * dx; o.fy += fr * dy; o.fz += fr * dz;
+        o.u += v;
+    } else {
+        o.u += pair_pot_at_zero(C.pot);
     }
-    o.w2 += w * w;
     if (LM == LIST_ALL || (LM == LIST_CROSS && cross)) {
         if (o.nn < C.nbr_cap) {
             C.nbr_j[(size_t)o.nn * N + i] = j;
@@ -434,8 +438,8 @@ __device__ __forceinline__ void force_finish(const Ctx<T>& C, int i, T half_dt, 
     vec_t<T> f;
     f.x = o.fx; f.y = o.fy; f.z = o.fz; f.w = T(0);
     C.F[i] = f;
-    // v(r) = (a r_c / 2) w^2 per pair, each pair seen from both sides
-    C.upot[i] = T(0.25) * C.a * C.rc * o.w2;
+    // each pair is seen from both sides
+    C.upot[i] = T(0.5) * o.u;
     if (kick) {
         vec_t<T> pv = C.pB[i];
         pv.x += half_dt * o.fx; pv.y += half_dt * o.fy; pv.z += half_dt * o.fz;
@@ -1199,7 +1203,6 @@ __global__ void k_obs_chunks(Ctx<T> C, const int* __restrict__ chunk_rep, const 
     const RepInfo& R = C.reps[rep];
     double acc[NTERMS];
     for (int k = 0; k < NTERMS; ++k) acc[k] = 0.0;
-    const double half_rc_a = 0.5 * (double)C.a * (double)C.rc;
     for (int i = chunk_begin[ch] + threadIdx.x; i < chunk_end[ch]; i += blockDim.x) {
         const vec_t<T> qi = C.qA[i];
         const vec_t<T> pi = C.pA[i];
@@ -1214,20 +1217,22 @@ __global__ void k_obs_chunks(Ctx<T> C, const int* __restrict__ chunk_rep, const 
         acc[9] += (e <= 0.0) ? 1.0 : 0.0;
         acc[10] += fin ? 0.0 : 1.0;
         if (fin) {
-            // per neighbour, in the step's precision: w = 1 - r/r_c and, for
-            // r > 0, the Laplacian term a/r_c - 2a w/r = 3a/r_c - 2a/r
-            T w2 = 0, inv_r = 0;
-            int npos = 0;
+            // per neighbour, in the step's precision: v(r) and, for r > 0, the
+            // Laplacian term v'' + 2 v'/r
+            T usum = 0, lsum = 0;
             for_each_neighbour(C, C.qA, i, qi, C.cA[i], R,
                                [&](int, const vec_t<T>&, T, T, T, T r2, bool) {
-                                   const T ir = r2 > T(0) ? trsqrt(r2) : T(0);
-                                   const T w = T(1) - r2 * ir * C.inv_rc;
-                                   w2 += w * w;
-                                   inv_r += ir;
-                                   npos += r2 > T(0) ? 1 : 0;
+                                   if (r2 > T(0)) {
+                                       T v, fr, lap;
+                                       pair_pot(C.pot, r2, trsqrt(r2), v, fr, lap);
+                                       usum += v;
+                                       lsum += lap;
+                                   } else {
+                                       usum += pair_pot_at_zero(C.pot);
+                                   }
                                });
-            acc[1] += 0.5 * half_rc_a * (double)w2;   // each pair is seen twice
-            acc[8] += 3.0 * (double)C.a / (double)C.rc * npos - 2.0 * (double)C.a * (double)inv_r;
+            acc[1] += 0.5 * (double)usum;   // each pair is seen twice
+            acc[8] += (double)lsum;
         }
     }
     __shared__ double sh[NTERMS][OBS_THREADS];

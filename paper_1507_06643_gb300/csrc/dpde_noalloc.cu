@@ -11,6 +11,7 @@
 // GPU (different streams, threads or devices' concurrent use of the same
 // device) race and must be serialised by the caller.
 #include "dpde.h"
+#include "dpde_device.cuh"
 
 #include <cmath>
 #include <cstring>
@@ -55,6 +56,7 @@ struct NaGeom {
     int nc[3];
     double rc, rc2, a, mass, cv;
     int n;
+    dpde::PotT<double> pot;
 };
 
 __device__ __forceinline__ int na_cell(const NaGeom& G, const double* q, int i, int d) {
@@ -150,13 +152,14 @@ __global__ void k_na_terms(NaGeom G, const double* __restrict__ q, const double*
                             r2 += v * v;
                         }
                         if (r2 >= G.rc2) continue;
-                        const double r = sqrt(r2);
-                        const double w = 1.0 - r / G.rc;
-                        u += 0.25 * G.a * G.rc * w * w;   // half of v(r): each pair is seen twice
-                        if (r > 0.0) {
-                            const double f = G.a * w / r;
-                            fx += f * d[0]; fy += f * d[1]; fz += f * d[2];
-                            lap += G.a / G.rc - 2.0 * G.a * w / r;
+                        if (r2 > 0.0) {
+                            double v, fr, lp;
+                            dpde::pair_pot(G.pot, r2, 1.0 / sqrt(r2), v, fr, lp);
+                            u += 0.5 * v;   // each pair is seen twice
+                            fx += fr * d[0]; fy += fr * d[1]; fz += fr * d[2];
+                            lap += lp;
+                        } else {
+                            u += 0.5 * dpde::pair_pot_at_zero(G.pot);
                         }
                     }
                 }
@@ -197,7 +200,9 @@ int dpde_observables_noalloc(const dpde_params* params, const dpde_replica* repl
     if (!params || !replica || !out) return na_fail(DPDE_ERR_ARG, "params, replica and out are required");
     const dpde_params& P = *params;
     const dpde_replica& Rp = *replica;
-    if (!(P.mass > 0) || !(P.r_cut > 0) || !(P.a >= 0) || !(Rp.cv > 0) || Rp.n < 0)
+    if (!(P.mass > 0) || !(P.r_cut > 0) || !(P.a >= 0) || !(Rp.cv > 0) || Rp.n < 0 ||
+        (P.potential != DPDE_POT_SOFT && P.potential != DPDE_POT_LJ) ||
+        (P.potential == DPDE_POT_LJ && (!(P.lj_eps >= 0) || !(P.lj_r > 0))))
         return na_fail(DPDE_ERR_ARG, "invalid parameters");
     if (Rp.n > NA_MAX_N)
         return na_fail(DPDE_ERR_ARG, "dpde_observables_noalloc: n = " + std::to_string(Rp.n) +
@@ -221,6 +226,7 @@ int dpde_observables_noalloc(const dpde_params* params, const dpde_replica* repl
     G.rc = P.r_cut;
     G.rc2 = P.r_cut * P.r_cut;
     G.a = P.a;
+    G.pot = dpde::make_pot(P.potential, P.a, P.r_cut, P.lj_eps, P.lj_r);
     G.mass = P.mass;
     G.cv = Rp.cv;
     G.n = (int)Rp.n;

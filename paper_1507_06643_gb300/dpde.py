@@ -40,7 +40,7 @@ class DPDEError(RuntimeError):
 class dpde_params(C.Structure):
     _fields_ = [("mass", C.c_double), ("r_cut", C.c_double), ("a", C.c_double),
                 ("sigma", C.c_double), ("seed", C.c_uint64), ("precision", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("potential", C.c_int32), ("lj_eps", C.c_double), ("lj_r", C.c_double)]
 
 
 class dpde_replica(C.Structure):
@@ -259,8 +259,13 @@ def dpde_debug_gaussian(seed, step, replica, id_a, id_b, precision="fp64") -> np
     return out
 
 
-def make_params(mass=1.0, r_cut=1.0, a=25.0, sigma=3.0, seed=0, precision="mixed") -> dpde_params:
-    return dpde_params(mass, r_cut, a, sigma, seed, PRECISIONS.get(precision, precision), 0)
+POT_SOFT, POT_LJ = 0, 1
+
+
+def make_params(mass=1.0, r_cut=1.0, a=25.0, sigma=3.0, seed=0, precision="mixed", potential=POT_SOFT,
+                lj_eps=1.0, lj_r=1.0) -> dpde_params:
+    return dpde_params(mass, r_cut, a, sigma, seed, PRECISIONS.get(precision, precision), potential,
+                       lj_eps, lj_r)
 
 
 def make_replica(n, box, cv, bricks=(1, 1, 1)) -> dpde_replica:

@@ -51,13 +51,13 @@ def make_state(specs, seed, float32):
     return np.concatenate(qs), np.concatenate(ps), np.concatenate(es)
 
 
-def oracle_cells(q, specs, offsets):
+def oracle_cells(q, specs, offsets, r_cut=1.0):
     """The oracle's cell coordinates c_d = min(nc_d - 1, (int)(x * (nc_d / L_d)))."""
     out = np.empty(q.shape, np.int64)
     for r, (n, box, cv, kT, br) in enumerate(specs):
         s = slice(offsets[r], offsets[r + 1])
         rep = O.make_replica(n, box, cv, br)
-        nc, _ = O.cell_grid(rep, 1.0)
+        nc, _ = O.cell_grid(rep, r_cut)
         for d in range(3):
             x = q[s, d] * (nc[d] / rep.box[d])
             out[s, d] = np.minimum(nc[d] - 1, np.maximum(0, np.trunc(x).astype(np.int64)))
@@ -65,21 +65,22 @@ def oracle_cells(q, specs, offsets):
 
 
 def run_both(specs, precision, scheme, nsteps, dt=0.01, seed=1, a=25.0, sigma=3.0, prm_seed=42,
-             use_graph=True, state=None):
+             use_graph=True, state=None, r_cut=1.0, pot=None):
     """Runs both sides step by step. Returns (errs, flips, gpu_state, ref) where
     flips is the set of particles whose cell differed between the two sides at
     some step (the per-step decision positions are the end-of-step positions)."""
     q, p, e = state if state is not None else make_state(specs, seed, precision == "mixed")
     reps = [dpde.make_replica(n, box, cv, br) for n, box, cv, _, br in specs]
-    S = dpde.System(dpde.make_params(1.0, 1.0, a, sigma, prm_seed, precision), reps)
+    pot = pot or {}
+    S = dpde.System(dpde.make_params(1.0, r_cut, a, sigma, prm_seed, precision, **pot), reps)
     S.set_state(q, p, e)
     oreps = [O.make_replica(n, box, cv, br) for n, box, cv, _, br in specs]
-    ref = O.System(oreps, O.make_params(1.0, 1.0, a, sigma, prm_seed), q, p, e)
+    ref = O.System(oreps, O.make_params(1.0, r_cut, a, sigma, prm_seed, **pot), q, p, e)
     flips = set()
     for _ in range(nsteps):
         S.step(1, dt, scheme, use_graph)
         ref.run(1, dt, scheme)
-        bad = np.any(S.get_cells() != oracle_cells(ref.q, specs, ref.offsets), axis=1)
+        bad = np.any(S.get_cells() != oracle_cells(ref.q, specs, ref.offsets, r_cut), axis=1)
         flips.update(np.nonzero(bad)[0].tolist())
     qg, pg, eg = S.get_state()
     obs_g = S.observables()

@@ -276,6 +276,53 @@ def test_ssa_launches_follow_colour_classes(box, bricks):
     S.close()
 
 
+# ---- splined Lennard-Jones potential, Eq. (Ep) -----------------------------------------
+
+LJ_POT = {"potential": 1, "lj_eps": 1.0, "lj_r": 1.0}
+
+
+def lj_case(cells, seed, precision):
+    from paper_1507_06643_gb300 import inputs
+    q, p, e, L = inputs.fcc_state(cells, 0.8095, 1.0, 50.0, 1.0, seed)
+    if precision == "mixed":
+        q = q.astype(np.float32).astype(np.float64)
+        q = np.where(q >= L, 0.0, q)
+        p = p.astype(np.float32).astype(np.float64)
+    return (q, p, e), L
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("scheme,bricks", [("SER", (1, 1, 1)), ("HYBRID", (2, 2, 2)), ("SSA", (1, 1, 1)),
+                                           ("SEM", (1, 1, 1))])
+def test_parity_lennard_jones(precision, scheme, bricks):
+    """An FCC crystal at the paper's density 0.8095 (8^3 cells, 2048
+    particles, r_cut = 2.5 r_LJ, sigma = 4), 10 steps of dt = 0.002."""
+    compared = 0
+    for seed in range(61, 69):
+        state, L = lj_case(8, seed, precision)
+        specs = [(len(state[0]), (L, L, L), 50.0, 1.0, bricks)]
+        errs, flips, (_, _, _, obs), ref = run_both(specs, precision, scheme, 10, dt=0.002, sigma=4.0,
+                                                   state=state, r_cut=2.5, pot=LJ_POT)
+        if flips and scheme in ("SSA", "HYBRID"):
+            continue
+        assert max(errs.values()) < TOL[precision], (seed, errs)
+        o = ref.observables(0)
+        for k in ("U", "Tpot_num", "Tpot_den"):
+            assert abs(obs[0][k] - o[k]) <= 10 * TOL[precision] * max(1.0, abs(o[k])), (k, obs[0][k], o[k])
+        compared += 1
+        if compared == 2:
+            break
+    assert compared >= 1
+
+
+def test_lj_rejects_bad_parameters():
+    from paper_1507_06643_gb300 import dpde
+    rep = [dpde.make_replica(500, (12.0, 12.0, 12.0), 50.0)]
+    for kw in ({"potential": 2}, {"potential": 1, "lj_r": 0.0}, {"potential": 1, "lj_eps": -1.0}):
+        with pytest.raises(dpde.DPDEError):
+            dpde.System(dpde.make_params(r_cut=2.5, **kw), rep)
+
+
 # ---- projection on the internal energies (Sec. IV.C) ----------------------------------
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
