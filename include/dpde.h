@@ -371,7 +371,8 @@ int dpde_set_tuning(dpde_handle* h, const dpde_tuning* t);
 /* Autotuner: times `steps` graph-replayed steps of `scheme` at `dt` (after
  * one untimed replay) for each candidate -- tile edges 4..8, then per-particle block sizes
  * 128, 256, 512, then SSA block sizes 32, 64, 128, each stage keeping the
- * best so far -- on the handle's current state, restoring that state, its
+ * best so far, a candidate replacing it only when more than 1% faster -- on
+ * the handle's current state, restoring that state, its
  * forces and its step counter after every trial; then applies the fastest
  * tuning and writes it to *out (host pointer, may be NULL). The state after
  * the call equals the state before it. Synchronous. steps in 1..1000. */

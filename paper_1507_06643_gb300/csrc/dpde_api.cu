@@ -59,6 +59,10 @@ struct dpde_handle {
     int* col_cells[2] = {nullptr, nullptr};
     std::vector<int> col_off[2];   // NCOLOURS + 1 offsets into col_cells
     int hcap = 0;             // halo particles staged per force tile
+    int hcap_dense = 0;       // ... per deferred (dense) tile
+    size_t tile_smem_dense = 0;
+    int* defer = nullptr;     // deferred tiles of the force pass: list, then count
+    int ndense_blocks = 0;
     int hcc = 0;              // halo cells per force tile, (tile_edge + 2)^3
     size_t tile_smem = 0;
     double per_cell_max = 0;  // mean particles per cell of the densest replica
@@ -160,13 +164,21 @@ void enqueue_sort(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T half_dt, T
 
 template <class T>
 void enqueue_force(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T half_dt, int kick, int list) {
-    const dim3 g(h->ntiles), blk(TILE_THREADS);
+    const dim3 g(h->ntiles), blk(TILE_THREADS), gd(h->ndense_blocks);
+    int* cnt = h->defer + h->ntiles;
+    cudaMemsetAsync(cnt, 0, sizeof(int), st);
+#define DPDE_FORCE(LMV)                                                                                          \
+    k_force_tile<T, LMV><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap,      \
+                                                       h->hcc, h->defer, cnt);                                   \
+    k_force_tile_dense<T, LMV><<<gd, blk, h->tile_smem_dense, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, \
+                                                                    h->hcap_dense, h->hcc, h->defer, cnt)
     switch (list) {
-    case LIST_ALL: k_force_tile<T, LIST_ALL><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap, h->hcc); break;
-    case LIST_CROSS: k_force_tile<T, LIST_CROSS><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap, h->hcc); break;
-    case LIST_FWD: k_force_tile<T, LIST_FWD><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap, h->hcc); break;
-    default: k_force_tile<T, LIST_NONE><<<g, blk, h->tile_smem, st>>>(C, h->tile_org, h->tile_dim, half_dt, kick, h->hcap, h->hcc); break;
+    case LIST_ALL: DPDE_FORCE(LIST_ALL); break;
+    case LIST_CROSS: DPDE_FORCE(LIST_CROSS); break;
+    case LIST_FWD: DPDE_FORCE(LIST_FWD); break;
+    default: DPDE_FORCE(LIST_NONE); break;
     }
+#undef DPDE_FORCE
 }
 
 // The SSA sequence: the Gaussians of every forward entry, then one launch per
@@ -276,7 +288,7 @@ void free_all(dpde_handle* h) {
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
     void* bufs[] = {h->qA, h->pA, h->qB, h->pB, h->F, h->dp, h->upot, h->proj_e0, h->proj_shift, h->proj_partial, h->eA, h->eB, h->nbr_w, h->cA, h->cB, h->nbr_j,
-                    h->nbr_n, h->fwd_j, h->fwd_w, h->fwd_g, h->fwd_n, h->tile_org, h->tile_dim, h->col_cells[0], h->col_cells[1], h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
+                    h->nbr_n, h->fwd_j, h->fwd_w, h->fwd_g, h->fwd_n, h->tile_org, h->tile_dim, h->defer, h->col_cells[0], h->col_cells[1], h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
                     h->rep_of_cell, h->brick_rep, h->tab, h->chunk_rep, h->chunk_begin, h->chunk_end,
                     h->rep_chunk_begin, h->partial, h->obs_out, h->d_reps, h->d_step, h->d_status,
                     h->staging, h->cells_out};
@@ -310,29 +322,55 @@ int set_tiles(dpde_handle* h, int edge) {
                                      (double)((smem_limit - thead) / tper));
     hcap &= ~3;   // keeps the arrays after the positions 16-byte aligned
     const size_t smem = 32 + thead + (size_t)hcap * tper;
+    // deferred tiles: 2.5x the mean halo (dense regions such as a shock front)
+    int hcap_dense = (int)std::min<double>(std::min<double>(2.5 * mean_halo + 64.0, 65535.0),
+                                           (double)((smem_limit + 24 * 1024 - thead) / tper));
+    hcap_dense = std::max(hcap_dense, hcap) & ~3;
+    const size_t smem_dense = 32 + thead + (size_t)hcap_dense * tper;
     if (h->tile_org) cudaFree(h->tile_org);
     if (h->tile_dim) cudaFree(h->tile_dim);
+    if (h->defer) cudaFree(h->defer);
     h->tile_org = h->tile_dim = nullptr;
+    h->defer = nullptr;
+    CK(h, cudaMalloc(&h->defer, sizeof(int) * (torg.size() + 1)));
     CK(h, cudaMalloc(&h->tile_org, sizeof(int4) * std::max<size_t>(1, torg.size())));
     CK(h, cudaMalloc(&h->tile_dim, sizeof(int4) * std::max<size_t>(1, tdim.size())));
     CK(h, cudaMemcpy(h->tile_org, torg.data(), sizeof(int4) * torg.size(), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->tile_dim, tdim.data(), sizeof(int4) * tdim.size(), cudaMemcpyHostToDevice));
-    const int sm = (int)smem;
+    const int sm = (int)smem, smd = (int)smem_dense;
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
     if (h->mixed) {
-        CK(h, cudaFuncSetAttribute(k_force_tile<float, LIST_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-        CK(h, cudaFuncSetAttribute(k_force_tile<float, LIST_ALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-        CK(h, cudaFuncSetAttribute(k_force_tile<float, LIST_CROSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-        CK(h, cudaFuncSetAttribute(k_force_tile<float, LIST_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        CK(h, cudaFuncSetAttribute(k_force_tile<float, LIST_NONE>, A, sm));
+        CK(h, cudaFuncSetAttribute(k_force_tile<float, LIST_ALL>, A, sm));
+        CK(h, cudaFuncSetAttribute(k_force_tile<float, LIST_CROSS>, A, sm));
+        CK(h, cudaFuncSetAttribute(k_force_tile<float, LIST_FWD>, A, sm));
+        CK(h, cudaFuncSetAttribute(k_force_tile_dense<float, LIST_NONE>, A, smd));
+        CK(h, cudaFuncSetAttribute(k_force_tile_dense<float, LIST_ALL>, A, smd));
+        CK(h, cudaFuncSetAttribute(k_force_tile_dense<float, LIST_CROSS>, A, smd));
+        CK(h, cudaFuncSetAttribute(k_force_tile_dense<float, LIST_FWD>, A, smd));
     } else {
-        CK(h, cudaFuncSetAttribute(k_force_tile<double, LIST_NONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-        CK(h, cudaFuncSetAttribute(k_force_tile<double, LIST_ALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-        CK(h, cudaFuncSetAttribute(k_force_tile<double, LIST_CROSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-        CK(h, cudaFuncSetAttribute(k_force_tile<double, LIST_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        CK(h, cudaFuncSetAttribute(k_force_tile<double, LIST_NONE>, A, sm));
+        CK(h, cudaFuncSetAttribute(k_force_tile<double, LIST_ALL>, A, sm));
+        CK(h, cudaFuncSetAttribute(k_force_tile<double, LIST_CROSS>, A, sm));
+        CK(h, cudaFuncSetAttribute(k_force_tile<double, LIST_FWD>, A, sm));
+        CK(h, cudaFuncSetAttribute(k_force_tile_dense<double, LIST_NONE>, A, smd));
+        CK(h, cudaFuncSetAttribute(k_force_tile_dense<double, LIST_ALL>, A, smd));
+        CK(h, cudaFuncSetAttribute(k_force_tile_dense<double, LIST_CROSS>, A, smd));
+        CK(h, cudaFuncSetAttribute(k_force_tile_dense<double, LIST_FWD>, A, smd));
     }
     h->ntiles = (int)torg.size();
     h->hcc = hcc;
     h->hcap = hcap;
     h->tile_smem = smem;
+    h->hcap_dense = hcap_dense;
+    h->tile_smem_dense = smem_dense;
+    int nsm = 152;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    h->ndense_blocks = std::max(1, std::min((int)torg.size(), nsm));
     h->tile_edge = edge;
     return DPDE_OK;
 }
@@ -809,7 +847,8 @@ int dpde_autotune(dpde_handle* h, int32_t scheme, double dt, int32_t steps, dpde
                 (stage == 0 ? t.tile_edge : (stage == 1 ? t.block : t.ssa_block)) = cand[c];
                 double ms = 0.0;
                 rc = trial(t, ms);
-                if (rc == DPDE_OK && ms < best_ms) {
+                // a candidate must beat the incumbent by more than the trial noise
+                if (rc == DPDE_OK && ms < 0.99 * best_ms) {
                     best_ms = ms;
                     best = t;
                 }

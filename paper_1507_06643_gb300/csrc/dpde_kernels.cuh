@@ -510,15 +510,18 @@ __host__ __device__ constexpr size_t tile_per_particle() {
     return sizeof(vec_t<T>) + 2 * sizeof(int) + sizeof(unsigned short);
 }
 
+// One tile on the calling block. A tile whose halo holds more than hcap
+// particles is appended to `defer` when that list is given (a second launch
+// with a larger capacity takes it), else computed through the global path.
 template <class T, int LM>
-__global__ void __launch_bounds__(TILE_THREADS) k_force_tile(Ctx<T> C, const int4* __restrict__ tile_org,
-                                                             const int4* __restrict__ tile_dim, T half_dt,
-                                                             int kick, int hcap, int hcc) {
+__device__ __forceinline__ void force_tile_run(const Ctx<T>& C, int tile, const int4* __restrict__ tile_org,
+                                               const int4* __restrict__ tile_dim, T half_dt, int kick, int hcap,
+                                               int hcc, int* defer, int* ndefer) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((size_t)smem_raw + 31) & ~(size_t)31);
     using vec = vec_t<T>;
-    const int4 org = tile_org[blockIdx.x];
-    const int4 dim = tile_dim[blockIdx.x];
+    const int4 org = tile_org[tile];
+    const int4 dim = tile_dim[tile];
     const RepInfo& R = C.reps[org.x];
     const int HX = dim.x + 2, HY = dim.y + 2, HZ = dim.z + 2;
     const int HC = HX * HY * HZ;
@@ -606,6 +609,10 @@ __global__ void __launch_bounds__(TILE_THREADS) k_force_tile(Ctx<T> C, const int
     }
     __syncthreads();
     if (!staged) {
+        if (defer) {
+            if (threadIdx.x == 0) defer[atomicAdd(ndefer, 1)] = tile;
+            return;
+        }
         // fallback: own particles through the global path
         for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
             const int h = ((r / dim.y + 1) * HY + (r % dim.y + 1)) * HX;
@@ -688,6 +695,29 @@ __global__ void __launch_bounds__(TILE_THREADS) k_force_tile(Ctx<T> C, const int
         }
         flush();
         if (act) force_finish<T, LM>(C, i, half_dt, kick, o);
+    }
+}
+
+template <class T, int LM>
+__global__ void __launch_bounds__(TILE_THREADS) k_force_tile(Ctx<T> C, const int4* __restrict__ tile_org,
+                                                             const int4* __restrict__ tile_dim, T half_dt,
+                                                             int kick, int hcap, int hcc, int* defer,
+                                                             int* ndefer) {
+    force_tile_run<T, LM>(C, blockIdx.x, tile_org, tile_dim, half_dt, kick, hcap, hcc, defer, ndefer);
+}
+
+// The deferred tiles (dense regions), persistent blocks with a larger halo
+// capacity; a tile beyond even that takes the global path.
+template <class T, int LM>
+__global__ void __launch_bounds__(TILE_THREADS) k_force_tile_dense(Ctx<T> C, const int4* __restrict__ tile_org,
+                                                                   const int4* __restrict__ tile_dim, T half_dt,
+                                                                   int kick, int hcap, int hcc,
+                                                                   const int* __restrict__ defer,
+                                                                   const int* __restrict__ ndefer) {
+    const int n = *ndefer;
+    for (int u = blockIdx.x; u < n; u += gridDim.x) {
+        force_tile_run<T, LM>(C, defer[u], tile_org, tile_dim, half_dt, kick, hcap, hcc, nullptr, nullptr);
+        __syncthreads();
     }
 }
 

@@ -144,6 +144,24 @@ def test_parity_dense_slab(precision, scheme, bricks):
     assert compared >= 1
 
 
+def test_parity_tiles_beyond_the_dense_capacity():
+    """Tile edge 2 and a slab at 2.9x the mean density: slab tiles overflow
+    both the regular and the dense halo capacity and take the global path."""
+    from oracle import oracle as O
+    from paper_1507_06643_gb300 import dpde
+    q, p, e = slab_state(5, L=24.0, rho=3.0, rho_slab=14.0, slab=4.0)
+    n, box = len(q), (24.0, 24.0, 24.0)
+    S = dpde.System(dpde.make_params(precision="fp64", seed=42), [dpde.make_replica(n, box, 50.0, (2, 2, 2))])
+    S.set_tuning(tile_edge=2)
+    S.set_state(q, p, e)
+    S.step(2, 0.01, "HYBRID")
+    qg, pg, eg = S.get_state()
+    S.close()
+    ref = O.System([O.make_replica(n, box, 50.0, (2, 2, 2))], O.make_params(seed=42), q, p, e)
+    ref.run(2, 0.01, "HYBRID")
+    assert rel_err(pg, ref.p) < TOL["fp64"] and rel_err(eg, ref.eps) < TOL["fp64"]
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("scheme", ["SER", "HYBRID", "SSA"])
 def test_parity_batched_replicas(precision, scheme):
