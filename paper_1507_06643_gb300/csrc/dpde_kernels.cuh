@@ -997,15 +997,23 @@ __global__ void k_ssa_gauss(Ctx<T> C) {
 // The pair map on (p_s, eps_s, beta_s) in registers and partner (p_t, eps_t)
 // with beta_t = p_t.w, for the entry (G, w) = g; returns the new partner
 // state, beta in .w.
+// x / y: exact in double; in float through the fast reciprocal (2 ulp), which
+// keeps the chains' critical path short
+__device__ __forceinline__ float ssa_div(float x, float y) { return __fdividef(x, y); }
+__device__ __forceinline__ double ssa_div(double x, double y) { return x / y; }
+__device__ __forceinline__ float ssa_beta(ff e, const RepInfo& R) { return __fdividef(R.cvf, e.hi); }
+__device__ __forceinline__ double ssa_beta(double e, const RepInfo& R) { return R.cv / e; }
+
+// k2 = 2 dt / m
 template <class T>
 __device__ __forceinline__ void ssa_pair_map(const Ctx<T>& C, const RepInfo& R, vec_t<T>& ps, eps_t<T>& es,
-                                             T& bs, vec_t<T>& pt, eps_t<T>& et, const vec_t<T>& g, T dt,
+                                             T& bs, vec_t<T>& pt, eps_t<T>& et, const vec_t<T>& g, T k2,
                                              T amp0) {
     const T w = g.w;
-    const T chi = w * w;
+    const T chik = w * w * k2;
     const T gam = C.sig2_4 * (bs + pt.w);
-    const T aa = T(2) * gam * chi * dt * C.inv_m;
-    const T amp = (gam != T(0)) ? C.sigma * tsqrt(C.m * (-texpm1(T(-2) * aa)) / gam) : amp0 * w;
+    const T aa = gam * chik;   // a = 2 gamma chi dt / m
+    const T amp = (gam != T(0)) ? C.sigma * tsqrt(ssa_div(C.m * (-texpm1(T(-2) * aa)), gam)) : amp0 * w;
     const T em1 = texpm1(-aa);
     const T Dx = T(0.5) * (em1 * (ps.x - pt.x) + amp * g.x);
     const T Dy = T(0.5) * (em1 * (ps.y - pt.y) + amp * g.y);
@@ -1018,15 +1026,15 @@ __device__ __forceinline__ void ssa_pair_map(const Ctx<T>& C, const RepInfo& R, 
                  (T(0.25) * C.inv_m);
     ps.x = snx; ps.y = sny; ps.z = snz;
     es = eps_add(es, -dK);
-    bs = beta_of(es, R);
+    bs = ssa_beta(es, R);
     pt.x = tnx; pt.y = tny; pt.z = tnz;
     et = eps_add(et, -dK);
-    pt.w = beta_of(et, R);
+    pt.w = ssa_beta(et, R);
 }
 
 // Plain (unpipelined) chain, for cells with more than SSA_ROWS rows.
 template <class T>
-__device__ void ssa_chain_plain(const Ctx<T>& C, const RepInfo& R, int b, int e, T dt, T amp0) {
+__device__ void ssa_chain_plain(const Ctx<T>& C, const RepInfo& R, int b, int e, T k2, T amp0) {
     const size_t cap = (size_t)C.nbr_cap;
     for (int s = b; s < e; ++s) {
         const int nf = C.fwd_n[s];
@@ -1039,7 +1047,7 @@ __device__ void ssa_chain_plain(const Ctx<T>& C, const RepInfo& R, int b, int e,
             const vec_t<T> g = C.fwd_g[(size_t)s * cap + m];
             vec_t<T> pt = C.pB[t];
             eps_t<T> et = C.eB[t];
-            ssa_pair_map(C, R, ps, es, bs, pt, et, g, dt, amp0);
+            ssa_pair_map(C, R, ps, es, bs, pt, et, g, k2, amp0);
             C.pB[t] = pt;
             C.eB[t] = et;
         }
@@ -1079,8 +1087,9 @@ __global__ void __launch_bounds__(SSA_THREADS_MAX) k_ssa_colour(Ctx<T> C, const 
     if (total == 0) return;
     const RepInfo& R = C.reps[C.rep_of_cell[c]];
     const T amp0 = T(2) * C.sigma * sqrt_dt;   // amplitude of the map as gamma -> 0
+    const T k2 = T(2) * dt * C.inv_m;
     if (nrow > SSA_ROWS) {
-        ssa_chain_plain(C, R, b, e, dt, amp0);
+        ssa_chain_plain(C, R, b, e, k2, amp0);
         return;
     }
     const size_t cap = (size_t)C.nbr_cap;
@@ -1094,61 +1103,78 @@ __global__ void __launch_bounds__(SSA_THREADS_MAX) k_ssa_colour(Ctx<T> C, const 
             nf = row_n[r * bdim + tid];
         }
     };
-    // entry 0
-    int s = row_s[tid];
-    vec_t<T> ps = C.pB[s];
-    eps_t<T> es = C.eB[s];
-    T bs = ps.w;
-    int t = C.fwd_j[(size_t)s * cap];
-    vec_t<T> g = C.fwd_g[(size_t)s * cap];
-    vec_t<T> pt = C.pB[t];
-    eps_t<T> et = C.eB[t];
-    // entry 1 (index and entry)
-    int r1 = 0, m1 = 0, n1 = row_n[tid];
-    advance(r1, m1, n1);
-    int s1 = row_s[r1 * bdim + tid];
-    int t1 = C.fwd_j[(size_t)s1 * cap + m1];
-    vec_t<T> g1 = C.fwd_g[(size_t)s1 * cap + m1];
+    // An entry of the chain: owner s, partner t, (G, w); the partner state,
+    // and on a row switch the new owner's state, loaded two entries ahead.
+    struct Ent {
+        int s, t;
+        vec_t<T> g, pt, ps;
+        eps_t<T> et, es;
+        bool sw;
+    };
+    auto load_index = [&](int r, int m, Ent& x) {
+        x.s = row_s[r * bdim + tid];
+        x.t = C.fwd_j[(size_t)x.s * cap + m];
+        x.g = C.fwd_g[(size_t)x.s * cap + m];
+    };
+    auto load_state = [&](Ent& x, int prev_s) {
+        x.pt = C.pB[x.t];
+        x.et = C.eB[x.t];
+        x.sw = x.s != prev_s;
+        if (x.sw) {
+            x.ps = C.pB[x.s];
+            x.es = C.eB[x.s];
+        }
+    };
+    // the last two partner writes (w1 newest): the only stores a value loaded
+    // two entries ahead can miss
+    int w1t = -1, w2t = -1;
+    vec_t<T> w1p, w2p;
+    eps_t<T> w1e, w2e;
+    auto patch = [&](int x, vec_t<T>& pv, eps_t<T>& ev) {
+        if (x == w2t) { pv = w2p; ev = w2e; }
+        if (x == w1t) { pv = w1p; ev = w1e; }
+    };
+    Ent e0, e1, e2;
+    int r = 0, m = 0, nfr = row_n[tid];
+    load_index(r, m, e0);
+    load_state(e0, -1);
+    advance(r, m, nfr);
+    load_index(r, m, e1);
+    load_state(e1, e0.s);
+    advance(r, m, nfr);
+    load_index(r, m, e2);
+    int s = -1;
+    vec_t<T> ps;
+    eps_t<T> es;
+    T bs = T(0);
     for (int k = 0; k < total; ++k) {
-        // index and entry of k + 2
-        int r2 = r1, m2 = m1, n2 = n1;
-        advance(r2, m2, n2);
-        const int s2 = row_s[r2 * bdim + tid];
-        const int t2 = C.fwd_j[(size_t)s2 * cap + m2];
-        const vec_t<T> g2 = C.fwd_g[(size_t)s2 * cap + m2];
-        // state of entry k + 1
-        const bool sw = s1 != s;
-        vec_t<T> pt1 = C.pB[t1];
-        eps_t<T> et1 = C.eB[t1];
-        vec_t<T> ps1 = ps;
-        eps_t<T> es1 = es;
-        if (sw) {
-            ps1 = C.pB[s1];
-            es1 = C.eB[s1];
-        }
-        // pair map of entry k
-        ssa_pair_map(C, R, ps, es, bs, pt, et, g, dt, amp0);
-        C.pB[t] = pt;
-        C.eB[t] = et;
-        if (t1 == t) {
-            pt1 = pt;
-            et1 = et;
-        }
-        if (sw) {
-            ps.w = bs;
-            C.pB[s] = ps;
-            C.eB[s] = es;
-            if (s1 == t) {
-                ps1 = pt;
-                es1 = et;
+        // index of entry k + 3, state of entry k + 2
+        advance(r, m, nfr);
+        Ent e3;
+        load_index(r, m, e3);
+        load_state(e2, e1.s);
+        // entry k becomes current: patch its loads with the writes they missed
+        patch(e0.t, e0.pt, e0.et);
+        if (e0.sw) {
+            if (s >= 0) {
+                ps.w = bs;
+                C.pB[s] = ps;
+                C.eB[s] = es;
             }
-            ps = ps1;
-            es = es1;
-            bs = ps1.w;
-            s = s1;
+            patch(e0.s, e0.ps, e0.es);
+            s = e0.s;
+            ps = e0.ps;
+            es = e0.es;
+            bs = ps.w;
         }
-        t = t1; g = g1; pt = pt1; et = et1;
-        r1 = r2; m1 = m2; n1 = n2; s1 = s2; t1 = t2; g1 = g2;
+        ssa_pair_map(C, R, ps, es, bs, e0.pt, e0.et, e0.g, k2, amp0);
+        C.pB[e0.t] = e0.pt;
+        C.eB[e0.t] = e0.et;
+        w2t = w1t; w2p = w1p; w2e = w1e;
+        w1t = e0.t; w1p = e0.pt; w1e = e0.et;
+        e0 = e1;
+        e1 = e2;
+        e2 = e3;
     }
     ps.w = bs;
     C.pB[s] = ps;
