@@ -105,6 +105,10 @@ class ClockSampler:
 def workload_and_scheme(args):
     from paper_1507_06643_gb300 import inputs
     w = inputs.WORKLOADS[args.workload](args.precision)
+    if args.bricks:
+        b = tuple(int(x) for x in args.bricks.split(","))
+        b = b * 3 if len(b) == 1 else b
+        w.replicas = [inputs.ReplicaSpec(r.n, r.box, r.cv, r.kT, b, r.vz_split) for r in w.replicas]
     return w
 
 
@@ -252,6 +256,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if w.precision == "mixed" else "f64",
         "data": "synthetic: uniform positions, Maxwellian momenta (kT=1), eps = C_v kT (1 +- 5%)",
         "config": {"workload": w.name, "n": n_tot, "scheme": args.scheme, "precision": w.precision,
+                   "pairs_per_particle": pair_counts(w)[0] / n_tot,
+                   "ssa_pair_fraction": pair_counts(w)[1] / pair_counts(w)[0] if args.scheme == "HYBRID" else None,
                    "dt": dt, "bricks": list(w.replicas[0].bricks), "l2": "inputs larger than L2 "
                    f"(state ~{n_tot * (48 if w.precision == 'mixed' else 104) / 1e6:.0f} MB)",
                    "parallelism": f"replicas x{world}",
@@ -340,6 +346,11 @@ def drift_run(args, stream):
                      "mean_Tkin": float(np.mean(tk)), "mean_Tint": float(np.mean(ti)),
                      "wall_s": el, "E": Es}
     # precision-induced part: both runs share the initial state and the noise
+    # drift rate: least-squares slope of (E^n - E^0)/|E^0| against time
+    for prec in ("mixed", "fp64"):
+        Es = np.asarray(out[prec]["E"])
+        tt = np.arange(len(Es)) * every * w.dt
+        out[prec]["alpha_per_unit_time"] = float(np.polyfit(tt, (Es - Es[0]) / abs(Es[0]), 1)[0]) if len(Es) > 2 else None
     em, ef = np.asarray(out["mixed"].pop("E")), np.asarray(out["fp64"].pop("E"))
     out["max_rel_drift_mixed_minus_fp64"] = float(np.max(np.abs((em - em[0]) - (ef - ef[0]))) / abs(ef[0]))
     out["sample_every"] = every
@@ -434,10 +445,18 @@ def main():
     ap.add_argument("--drift-steps", type=int, default=10000,
                     help="measured steps of the energy-drift run on the 108k fluid (0: skip)")
     ap.add_argument("--drift-equil", type=int, default=2000)
+    ap.add_argument("--drift-only", action="store_true",
+                    help="run only the energy-drift study and print its JSON")
+    ap.add_argument("--bricks", default="",
+                    help="override the Hybrid brick grid: B or Bx,By,Bz")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
+    elif args.drift_only:
+        import torch
+        stream = torch.cuda.Stream()
+        print(json.dumps({"energy_drift": drift_run(args, stream)}))
     else:
         run_ours(args)
 
