@@ -118,7 +118,15 @@ def workload_and_scheme(args):
 # SSA pair map ~130 (2 expm1, 1 div, 1 sqrt, momenta, dK, two compensated eps
 # updates, two beta divisions); SER sweep 1 ~40, sweep 2 ~55 pair arithmetic.
 OPS_GAUSS = 180.0
-OPS_PER_PAIR = {"ssa": OPS_GAUSS + 130.0, "sweep1": OPS_GAUSS + 40.0, "sweep2": OPS_GAUSS + 55.0}
+OPS_PER_PAIR = {"ssa": 130.0, "ssa_gauss": OPS_GAUSS, "sweep1": OPS_GAUSS + 40.0, "sweep2": OPS_GAUSS + 55.0}
+KERNEL_OF_PHASE = {"ssa": "k_ssa_colour", "ssa_gauss": "k_ssa_gauss", "sweep1": "k_ser_sweep1",
+                   "sweep2": "k_ser_sweep2", "force": "k_force_tile", "gather": "k_rank_gather",
+                   "kick_drift": "k_kick_drift_key"}
+
+# DRAM bytes (read + write) per launch of a kernel from an ncu capture of the
+# named configuration (profiles/launches_large_n4m_hybrid_mixed.md); reported
+# only for that configuration and kernel.
+MEASURED_TRAFFIC = {("large_n4m", "HYBRID", "mixed", "k_ssa_colour"): 144.92e6}
 
 
 def pair_counts(w):
@@ -147,6 +155,7 @@ def algorithmic_model(w, phase: str, scheme: str, precision: str):
     total, intra = pair_counts(w)
     pairs = {"ssa": intra if scheme == "HYBRID" else total,
              "sweep1": total - intra if scheme == "HYBRID" else total}
+    pairs["ssa_gauss"] = pairs["ssa"]
     pairs["sweep2"] = pairs["sweep1"]
     state_bytes = 16 if precision == "mixed" else 32
     if phase in OPS_PER_PAIR:
@@ -246,8 +255,13 @@ def run_ours(args):
     else:
         peak = float(peaks["hbm_gbs"])
         peak_note = f"{peak_src} hbm_gbs"
-    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_note}
+    kernel = KERNEL_OF_PHASE.get(dom, dom)
+    traffic = MEASURED_TRAFFIC.get((w.name, args.scheme, w.precision, kernel))
+    if args.bricks:
+        traffic = None
+    roofline = {"bound": bound, "kernel": kernel, "phase": dom, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+                "peak_source": peak_note}
 
     drift = abs(obs1[0]["E"] - obs0[0]["E"]) / abs(obs0[0]["E"])
     out = {

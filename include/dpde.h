@@ -318,11 +318,12 @@ const char* dpde_noalloc_last_error(void);
 #define DPDE_PHASE_SCAN        1  /* prefix sum of the cell counts         */
 #define DPDE_PHASE_GATHER      2  /* scatter + (cell, id) rank + gather    */
 #define DPDE_PHASE_FORCE       3  /* forces + second half-kick             */
-#define DPDE_PHASE_SSA         4  /* SSA rounds (Hybrid set A, or SSA)      */
+#define DPDE_PHASE_SSA         4  /* SSA chains (Hybrid set A, or SSA)      */
 #define DPDE_PHASE_SWEEP1      5  /* SER first sweep                       */
 #define DPDE_PHASE_SWEEP2      6  /* SER second sweep / SEM sweep / copy   */
-#define DPDE_PHASE_OTHER       7  /* beta refresh, step counter            */
-#define DPDE_NUM_PHASES        8
+#define DPDE_PHASE_OTHER       7  /* projection on the internal energies   */
+#define DPDE_PHASE_SSA_GAUSS   8  /* Gaussians of the SSA pairs            */
+#define DPDE_NUM_PHASES        9
 
 /* Runs n steps like dpde_step without a graph, with CUDA events recorded on
  * the handle's stream around each phase; adds each phase's total elapsed

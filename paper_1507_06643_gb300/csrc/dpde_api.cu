@@ -186,13 +186,17 @@ void enqueue_force(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T half_dt, 
 template <class T>
 void enqueue_ssa(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_dt, int whole) {
     const std::vector<int>& off = h->col_off[whole];
+    phase(h, st, DPDE_PHASE_SSA_GAUSS, 0);
     k_ssa_gauss<T><<<ceil_div(h->N, 256), 256, 0, st>>>(C);
+    phase(h, st, DPDE_PHASE_SSA_GAUSS, 1);
+    phase(h, st, DPDE_PHASE_SSA, 0);
     for (int k = 0; k < NCOLOURS; ++k) {
         const int n = off[k + 1] - off[k];
         if (n > 0)
             k_ssa_colour<T><<<ceil_div(n, h->ssa_block), h->ssa_block, ssa_smem_bytes(h->ssa_block), st>>>(
                 C, h->col_cells[whole] + off[k], n, dt, sqrt_dt);
     }
+    phase(h, st, DPDE_PHASE_SSA, 1);
 }
 
 template <class T>
@@ -206,9 +210,7 @@ void enqueue_step(dpde_handle* h, cudaStream_t st, double dt_d, int scheme) {
     enqueue_force<T>(h, C, st, half_dt, 1, list);
     phase(h, st, DPDE_PHASE_FORCE, 1);
     if (scheme == DPDE_HYBRID || scheme == DPDE_SSA) {
-        phase(h, st, DPDE_PHASE_SSA, 0);
         enqueue_ssa<T>(h, C, st, dt, sqrt_dt, scheme == DPDE_SSA ? 1 : 0);
-        phase(h, st, DPDE_PHASE_SSA, 1);
     }
     if (scheme == DPDE_SER || scheme == DPDE_HYBRID) {
         phase(h, st, DPDE_PHASE_SWEEP1, 0);

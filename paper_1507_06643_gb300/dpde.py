@@ -75,7 +75,7 @@ EXPORTS = ["dpde_create", "dpde_set_state", "dpde_get_state", "dpde_step", "dpde
            "dpde_checkpoint", "dpde_restore", "dpde_observables_noalloc", "dpde_noalloc_last_error",
            "dpde_step_launches", "dpde_get_tuning", "dpde_set_tuning", "dpde_autotune",
            "dpde_set_projection"]
-PHASES = ["kick_drift", "scan", "gather", "force", "ssa", "sweep1", "sweep2", "other"]
+PHASES = ["kick_drift", "scan", "gather", "force", "ssa", "sweep1", "sweep2", "other", "ssa_gauss"]
 
 
 def lib():

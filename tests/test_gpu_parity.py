@@ -396,6 +396,21 @@ def test_projection_holds_the_energy(precision, tol):
     S.close()
 
 
+def test_step_profiled_reports_each_phase():
+    from paper_1507_06643_gb300 import dpde
+    specs = [(20000, (cube(20000),) * 3, 50.0, 1.0, (3, 3, 3))]
+    q, p, e = make_state(specs, 3, True)
+    S = dpde.System(dpde.make_params(precision="mixed"), [dpde.make_replica(*specs[0][:3], (3, 3, 3))])
+    S.set_state(q, p, e)
+    ph = S.step_profiled(2, 0.01, "HYBRID")
+    assert set(ph) == set(dpde.PHASES)
+    for k in ("kick_drift", "scan", "gather", "force", "ssa", "ssa_gauss", "sweep1", "sweep2"):
+        assert ph[k] > 0, k
+    assert ph["other"] == 0          # no projection
+    assert dpde.dpde_get_step(S.h) == 2
+    S.close()
+
+
 # ---- tuning -------------------------------------------------------------------------
 
 def _run_tuned(precision, tuning, steps=5, scheme="HYBRID"):
