@@ -30,10 +30,11 @@ template <class T> struct Ctx {
     T* nbr_w;        // 1 - r/r_cut of each entry
     int* nbr_n;      // entries per particle
     int nbr_cap;
-    int* fwd_j;      // forward pairs of the SSA, particle-major rows [i * nbr_cap + k],
-                     //   partner slots in SSA sequence order (segment, id)
+    int* fwd_j;      // forward pairs of the SSA as the force pass writes them, entry-major
+                     //   [k * N + i], partner slots in SSA sequence order (segment, id)
     T* fwd_w;        //   w = 1 - r/r_cut of each entry
-    vec* fwd_g;      //   (G_it, w) of each entry, drawn before the SSA launches
+    vec* fwd_g;      // (G_it, w) of each entry, particle-major [i * nbr_cap + k] (the SSA
+                     //   chains' reading order), drawn before the SSA launches
     int* fwd_n;
     const int* rep_of_slot;
     const int* rep_of_cell;
@@ -418,7 +419,7 @@ __device__ __forceinline__ void force_hit(const Ctx<T>& C, int i, int j, bool fw
         ++o.nn;
     } else if ((LM == LIST_CROSS || LM == LIST_FWD) && fwd) {
         if (o.nf < C.nbr_cap) {
-            const size_t at = (size_t)i * C.nbr_cap + o.nf;
+            const size_t at = (size_t)o.nf * N + i;
             C.fwd_j[at] = j;
             C.fwd_w[at] = w;
         }
@@ -954,7 +955,9 @@ constexpr int SSA_THREADS_MAX = 128;
 constexpr int SSA_ROWS = 20;     // rows per cell held in the shared row table
 constexpr int NCOLOURS = 75;     // (2 + 1) x (3 + 2) x (3 + 2) cell colours
 
-// G of every forward entry, with its weight: (G_st, w) at [s * cap + m]. A
+// G of every forward entry, with its weight: reads entry m of particle s at
+// [m * N + s] (as the force pass wrote it) and writes (G_st, w)
+// particle-major at [s * cap + m], the order the SSA chains read it. A
 // warp takes 32 consecutive particles and spreads their entries over its
 // lanes (a shuffle prefix sum of the row lengths gives each entry's owner).
 template <class T>
@@ -984,12 +987,13 @@ __global__ void k_ssa_gauss(Ctx<T> C) {
         const int excl = __shfl_sync(0xffffffffu, incl - nf, lo);
         if (f < total) {
             const int so = base + lo;
-            const size_t at = (size_t)so * cap + (f - excl);
+            const size_t at = (size_t)(f - excl) * C.N + so;
+            const size_t row = (size_t)so * cap + (f - excl);
             const int t = C.fwd_j[at];
             const T3<T> G = pair_gauss<T>(C.seed, step, (uint32_t)C.rep_of_slot[so], C.idB[so], C.idB[t]);
             vec_t<T> g;
             g.x = G.x; g.y = G.y; g.z = G.z; g.w = C.fwd_w[at];
-            C.fwd_g[at] = g;
+            C.fwd_g[row] = g;
         }
     }
 }
@@ -1043,7 +1047,7 @@ __device__ void ssa_chain_plain(const Ctx<T>& C, const RepInfo& R, int b, int e,
         eps_t<T> es = C.eB[s];
         T bs = ps.w;
         for (int m = 0; m < nf; ++m) {
-            const int t = C.fwd_j[(size_t)s * cap + m];
+            const int t = C.fwd_j[(size_t)m * C.N + s];
             const vec_t<T> g = C.fwd_g[(size_t)s * cap + m];
             vec_t<T> pt = C.pB[t];
             eps_t<T> et = C.eB[t];
@@ -1113,7 +1117,7 @@ __global__ void __launch_bounds__(SSA_THREADS_MAX) k_ssa_colour(Ctx<T> C, const 
     };
     auto load_index = [&](int r, int m, Ent& x) {
         x.s = row_s[r * bdim + tid];
-        x.t = C.fwd_j[(size_t)x.s * cap + m];
+        x.t = C.fwd_j[(size_t)m * C.N + x.s];
         x.g = C.fwd_g[(size_t)x.s * cap + m];
     };
     auto load_state = [&](Ent& x, int prev_s) {
