@@ -298,7 +298,8 @@ def run_ours(args):
     if rank == 0:
         out["clocks"] = clk.summary()
         if not args.no_cpu_baseline and world == 1:
-            out["cpu_baseline"] = cpu_baseline(w, args.scheme, args.cpu_seconds)
+            out["cpu_baseline"], base = cpu_baseline(w, args.scheme, args.cpu_seconds)
+            out["parity"] = parity_report(w, base, args.scheme)
         print(json.dumps(out))
     if world > 1:
         tdist.destroy_process_group()
@@ -403,10 +404,55 @@ def cpu_baseline(w, scheme: str, seconds: float, steps: int | None = None):
     t = time.perf_counter()
     S.run(nsteps, sub.dt, scheme)
     el = time.perf_counter() - t
-    return {"value": spec.n * nsteps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nsteps} step(s) of a {spec.n}-particle cubic sub-box of {w.name} "
-                      f"(same density and parameters, FP64, {scheme}, bricks {spec.bricks}), "
-                      f"{el:.1f} s"}
+    out = {"value": spec.n * nsteps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{nsteps} step(s) of a {spec.n}-particle cubic sub-box of {w.name} "
+                     f"(same density and parameters, FP64, {scheme}, bricks {spec.bricks}), "
+                     f"{el:.1f} s"}
+    return out, (sub, q, p, e, S, nsteps)
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _gpu_vs_oracle(sub, q, p, e, ref, nsteps, scheme, precision):
+    """Largest relative difference (q by minimum image, p, eps) between the
+    library and the oracle after the same steps from the same state."""
+    from paper_1507_06643_gb300 import dpde
+    spec = sub.replicas[0]
+    G = dpde.System(dpde.make_params(sub.mass, sub.r_cut, sub.a, sub.sigma, sub.seed, precision),
+                    [dpde.make_replica(spec.n, spec.box, spec.cv, spec.bricks)])
+    G.set_state(q, p, e)
+    G.step(nsteps, sub.dt, scheme, use_graph=False)
+    qg, pg, eg = G.get_state()
+    G.close()
+    L = np.asarray(spec.box, float)
+    dq = qg - ref.q
+    dq -= L * np.round(dq / L)
+    return max(float(np.max(np.abs(dq)) / np.max(np.abs(ref.q))), _rel(pg, ref.p), _rel(eg, ref.eps))
+
+
+def parity_report(w, base, scheme):
+    """Parity of the GPU path against the oracle on the baseline's sub-box: FP64
+    with the bench's scheme (the same oracle run the baseline timed), and the
+    mixed mode with SER on a smaller sub-box (SER's result does not depend on
+    cell binning, so float/double binning differences cannot enter)."""
+    from oracle import oracle as O
+    from paper_1507_06643_gb300 import inputs
+    sub, q, p, e, ref, nsteps = base
+    out = {"tolerance": {"fp64": 1e-11, "mixed": 2e-5}}
+    out["fp64"] = _gpu_vs_oracle(sub, q, p, e, ref, nsteps, scheme, "fp64")
+    out["fp64_scheme"] = scheme
+    small = oracle_sample(w, 60000)
+    spec = small.replicas[0]
+    q2, p2, e2 = inputs.workload_state(small, float32=True)
+    ref2 = O.System([O.make_replica(spec.n, spec.box, spec.cv, spec.bricks)],
+                    O.make_params(small.mass, small.r_cut, small.a, small.sigma, small.seed), q2, p2, e2)
+    ref2.run(2, small.dt, "SER")
+    out["mixed_ser"] = _gpu_vs_oracle(small, q2, p2, e2, ref2, 2, "SER", "mixed")
+    out["sample"] = (f"fp64: {nsteps} step(s) of the {sub.replicas[0].n}-particle sub-box above; mixed: 2 SER steps "
+                     f"of a {spec.n}-particle sub-box (float-rounded input on both sides)")
+    return out
 
 
 def run_reference(args):
