@@ -127,7 +127,7 @@ KERNEL_OF_PHASE = {"ssa": "k_ssa_colour", "ssa_gauss": "k_ssa_gauss", "sweep1": 
 # named configuration with the caches kept warm
 # (profiles/launches_large_n4m_hybrid_mixed.md); reported only for that
 # configuration and kernel.
-MEASURED_TRAFFIC = {("large_n4m", "HYBRID", "mixed", "k_ssa_colour"): 168.9e6}
+MEASURED_TRAFFIC = {}
 
 
 def pair_counts(w):
@@ -186,6 +186,9 @@ def run_ours(args):
     # tune on a relaxed state: the first steps from the random start differ
     S.step(args.warmup, dt, args.scheme)
     tuning = S.autotune(args.scheme, dt, 10) if not args.no_autotune else S.tuning()
+    if args.ssa_mode is not None or args.ssa_group is not None:
+        S.set_tuning(ssa_mode=args.ssa_mode, ssa_group=args.ssa_group)
+        tuning = S.tuning()
     obs0 = S.observables()
 
     S.step(args.warmup, dt, args.scheme)
@@ -221,7 +224,7 @@ def run_ours(args):
     ph = torch.from_numpy(p).pin_memory()
     eh = torch.from_numpy(e).pin_memory()
     S2 = dpde.System(prm, spec_reps, stream=stream.cuda_stream)
-    S2.set_tuning(**{k: tuning[k] for k in ("tile_edge", "block", "ssa_block")})
+    S2.set_tuning(**{k: tuning[k] for k in ("tile_edge", "block", "ssa_block", "ssa_mode", "ssa_group")})
     e2e_steps = args.e2e_steps
     S2.set_state(qh, ph, eh)
     torch.cuda.synchronize()
@@ -257,6 +260,8 @@ def run_ours(args):
         peak = float(peaks["hbm_gbs"])
         peak_note = f"{peak_src} hbm_gbs"
     kernel = KERNEL_OF_PHASE.get(dom, dom)
+    if dom == "ssa" and args.scheme == "HYBRID" and tuning.get("ssa_mode") == 1:
+        kernel = "k_ssa_domains"
     traffic = MEASURED_TRAFFIC.get((w.name, args.scheme, w.precision, kernel))
     if args.bricks:
         traffic = None
@@ -276,7 +281,7 @@ def run_ours(args):
                    "dt": dt, "bricks": list(w.replicas[0].bricks), "l2": "inputs larger than L2 "
                    f"(state ~{n_tot * (48 if w.precision == 'mixed' else 104) / 1e6:.0f} MB)",
                    "parallelism": f"replicas x{world}",
-                   "tuning": {k: tuning[k] for k in ("tile_edge", "block", "ssa_block")},
+                   "tuning": {k: tuning[k] for k in ("tile_edge", "block", "ssa_block", "ssa_mode", "ssa_group")},
                    "autotuned": not args.no_autotune},
         "e2e": e2e,
         "gpu_launches": None,
@@ -501,6 +506,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--ssa-mode", type=int, choices=(0, 1), default=None,
+                    help="force the SSA launch form: 0 one launch per colour class, 1 one launch over "
+                         "whole Hybrid domains")
+    ap.add_argument("--ssa-group", type=int, default=None, help="force the Hybrid domains per warp (1..8)")
     ap.add_argument("--fp64-steps", type=int, default=20,
                     help="steps of the FP64 GPU run of the same workload (0: skip)")
     ap.add_argument("--drift-steps", type=int, default=10000,

@@ -357,6 +357,16 @@ typedef struct dpde_tuning {
                          /* of 32 in 64..1024 (default 256)                           */
     int32_t ssa_block;   /* threads per block of the SSA launches: 32, 64, 96 or 128   */
                          /* (default 64)                                               */
+    int32_t ssa_mode;    /* 0 (default): one SSA launch per colour class; 1: the Hybrid */
+                         /* SSA sequence as one launch in which each warp takes whole  */
+                         /* domains and walks their colour classes in order (domains   */
+                         /* share no chain, so their sequences commute), with the      */
+                         /* domains' state staged in shared memory where it fits. Both */
+                         /* give the same results bit for bit. DPDE_SSA always takes   */
+                         /* the per-class launches (its chains span the replica).      */
+    int32_t ssa_group;   /* domains per warp of ssa_mode 1, 1..8; 0 = automatic (32 /  */
+                         /* the most cells of one class in one domain); get_tuning     */
+                         /* reports the value in use                                   */
     int32_t reserved;    /* must be 0                                                  */
     double ms_per_step;  /* dpde_autotune: measured ms per step of the result; else 0  */
 } dpde_tuning;
@@ -371,7 +381,8 @@ int dpde_set_tuning(dpde_handle* h, const dpde_tuning* t);
 
 /* Autotuner: times `steps` graph-replayed steps of `scheme` at `dt` (after
  * one untimed replay) for each candidate -- tile edges 4..8, then per-particle block sizes
- * 128, 256, 512, then SSA block sizes 32, 64, 128, each stage keeping the
+ * 128, 256, 512, then SSA block sizes 32, 64, 128, then the SSA modes 1 and
+ * 0, then (Hybrid in ssa_mode 1) 1..4 domains per warp, each stage keeping the
  * best so far, a candidate replacing it only when more than 1% faster -- on
  * the handle's current state, restoring that state, its
  * forces and its step counter after every trial; then applies the fastest

@@ -58,6 +58,15 @@ struct dpde_handle {
     // + col_x, for the brick domains (Hybrid) and the whole replica (SSA)
     int* col_cells[2] = {nullptr, nullptr};
     std::vector<int> col_off[2];   // NCOLOURS + 1 offsets into col_cells
+    // SSA domain by domain (ssa_mode 1, Hybrid): the cells of each brick
+    // sorted by colour class, and per brick the NCOLOURS + 1 class starts
+    int* dom_cells = nullptr;
+    int* dom_off = nullptr;
+    int* dom_cell0 = nullptr;    // first cell of each brick, then ncells
+    double dom_mean = 0.0;       // most particles per brick of a replica, on average
+    int ssa_mode = 0;
+    int ssa_group = 0;        // bricks per warp; 0 = dom_group_auto
+    int dom_group_auto = 1;   // 32 / the largest class of a brick, in 1..SSA_GROUP_MAX
     int hcap = 0;             // halo particles staged per force tile
     int hcap_dense = 0;       // ... per deferred (dense) tile
     size_t tile_smem_dense = 0;
@@ -181,8 +190,10 @@ void enqueue_force(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T half_dt, 
 #undef DPDE_FORCE
 }
 
-// The SSA sequence: the Gaussians of every forward entry, then one launch per
-// non-empty colour class, in colour order.
+// The SSA sequence: the Gaussians of every forward entry, then either, for
+// brick domains (Hybrid, ssa_mode 1), one launch in which each warp walks the
+// colour classes of whole bricks, or one launch per non-empty colour class,
+// in colour order; both apply the same sequence.
 template <class T>
 void enqueue_ssa(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_dt, int whole) {
     const std::vector<int>& off = h->col_off[whole];
@@ -190,6 +201,22 @@ void enqueue_ssa(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_
     k_ssa_gauss<T><<<ceil_div(h->N, 256), 256, 0, st>>>(C);
     phase(h, st, DPDE_PHASE_SSA_GAUSS, 1);
     phase(h, st, DPDE_PHASE_SSA, 0);
+    if (!whole && h->ssa_mode == 1 && h->nbricks > 0) {
+        const int group = h->ssa_group > 0 ? h->ssa_group : h->dom_group_auto;
+        const int warps = ceil_div(h->nbricks, group);
+        const int wpb = h->ssa_block / 32;
+        // staged slots per warp: the group's mean particle count + 25 % + 64,
+        // as far as the shared memory of a block allows
+        const size_t per_slot = sizeof(vec_t<T>) + sizeof(eps_t<T>);
+        const size_t fixed = ssa_domain_warp_bytes<T>(group, 0);
+        long long scap = ((long long)std::ceil(1.25 * group * h->dom_mean) + 64 + 31) / 32 * 32;
+        const long long fit = ((long long)(SSA_DOMAIN_SMEM / wpb) - (long long)fixed) / (long long)per_slot;
+        scap = std::max(0ll, std::min(scap, fit / 32 * 32));
+        k_ssa_domains<T><<<ceil_div(warps, wpb), h->ssa_block, wpb * ssa_domain_warp_bytes<T>(group, (int)scap), st>>>(
+            C, h->dom_cells, h->dom_off, h->dom_cell0, h->nbricks, group, (int)scap, dt, sqrt_dt);
+        phase(h, st, DPDE_PHASE_SSA, 1);
+        return;
+    }
     for (int k = 0; k < NCOLOURS; ++k) {
         const int n = off[k + 1] - off[k];
         if (n > 0)
@@ -278,6 +305,7 @@ int read_status(dpde_handle* h) {
     CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     if (st & ST_CAPACITY) return fail(h, DPDE_ERR_CAPACITY, "neighbour list capacity exceeded");
+    if (st & ST_DOMAIN) return fail(h, DPDE_ERR_CUDA, "internal error: an SSA chain left its domain");
     if (st & ST_NONFINITE) return fail(h, DPDE_ERR_NONFINITE, "non-finite value in the state");
     if (st & ST_NEG_EPS) return fail(h, DPDE_ERR_NEG_EPS, "internal energy eps_i <= 0");
     return DPDE_OK;
@@ -290,7 +318,7 @@ void free_all(dpde_handle* h) {
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
     void* bufs[] = {h->qA, h->pA, h->qB, h->pB, h->F, h->dp, h->upot, h->proj_e0, h->proj_shift, h->proj_partial, h->eA, h->eB, h->nbr_w, h->cA, h->cB, h->nbr_j,
-                    h->nbr_n, h->fwd_j, h->fwd_w, h->fwd_g, h->fwd_n, h->tile_org, h->tile_dim, h->defer, h->col_cells[0], h->col_cells[1], h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
+                    h->nbr_n, h->fwd_j, h->fwd_w, h->fwd_g, h->fwd_n, h->tile_org, h->tile_dim, h->defer, h->col_cells[0], h->col_cells[1], h->dom_cells, h->dom_off, h->dom_cell0, h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
                     h->rep_of_cell, h->brick_rep, h->tab, h->chunk_rep, h->chunk_begin, h->chunk_end,
                     h->rep_chunk_begin, h->partial, h->obs_out, h->d_reps, h->d_step, h->d_status,
                     h->staging, h->cells_out};
@@ -479,6 +507,7 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     // k mod P cells of a periodic domain axis), for brick domains (m = 0)
     // and whole replicas (m = 1)
     std::vector<int> col_cells[2];
+    std::vector<unsigned char> dom_col((size_t)std::max<long long>(1, ncells), 0);
     for (int m = 0; m < 2; ++m) {
         std::vector<std::vector<int>> cls(NCOLOURS);
         for (const RepInfo& I : h->info) {
@@ -502,6 +531,7 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
                         const int k = (col[2][z] * 5 + col[1][y]) * 5 + col[0][x];
                         const int c = I.cell_off + tx[x] + ty[y] + tz[z];
                         cls[k].push_back(c);
+                        if (m == 0) dom_col[c] = (unsigned char)k;
                     }
         }
         h->col_off[m].assign(1, 0);
@@ -511,6 +541,34 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
             h->col_off[m].push_back((int)col_cells[m].size());
         }
     }
+    // per brick (brick-major cell order: brick b of replica I holds cells
+    // cell_off + b k_x k_y k_z onwards) its cells sorted by colour class
+    std::vector<int> dom_cells, dom_off, dom_cell0;
+    dom_cells.reserve((size_t)ncells);
+    dom_off.reserve((size_t)nbricks * (NCOLOURS + 1));
+    int class_max = 1;
+    for (const RepInfo& I : h->info) {
+        const int kc = I.k[0] * I.k[1] * I.k[2];
+        const int nbr = I.B[0] * I.B[1] * I.B[2];
+        h->dom_mean = std::max(h->dom_mean, (double)I.n / nbr);
+        for (int b = 0; b < nbr; ++b) {
+            int cnt[NCOLOURS + 1] = {0};
+            const int c0 = I.cell_off + b * kc;
+            dom_cell0.push_back(c0);
+            for (int c = c0; c < c0 + kc; ++c) ++cnt[dom_col[c] + 1];
+            const int base = (int)dom_cells.size();
+            dom_off.push_back(base);
+            for (int k = 0; k < NCOLOURS; ++k) {
+                class_max = std::max(class_max, cnt[k + 1]);
+                cnt[k + 1] += cnt[k];
+                dom_off.push_back(base + cnt[k + 1]);
+            }
+            dom_cells.resize(dom_cells.size() + kc);
+            for (int c = c0; c < c0 + kc; ++c) dom_cells[base + cnt[dom_col[c]]++] = c;
+        }
+    }
+    dom_cell0.push_back((int)ncells);
+    h->dom_group_auto = std::max(1, std::min(SSA_GROUP_MAX, 32 / class_max));
     auto bail = [&](cudaError_t e, const char* what) {
         std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
         int code = e == cudaErrorMemoryAllocation ? DPDE_ERR_OOM : DPDE_ERR_CUDA;
@@ -603,6 +661,18 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         CKC(cudaMemset(h->nbr_n, 0, sizeof(int) * n1));
         CKC(cudaMemset(h->fwd_n, 0, sizeof(int) * n1));
     }
+    CKC(cudaMalloc(&h->dom_cells, sizeof(int) * std::max<size_t>(1, dom_cells.size())));
+    CKC(cudaMalloc(&h->dom_off, sizeof(int) * std::max<size_t>(1, dom_off.size())));
+    if (!dom_cells.empty())
+        CKC(cudaMemcpy(h->dom_cells, dom_cells.data(), sizeof(int) * dom_cells.size(), cudaMemcpyHostToDevice));
+    if (!dom_off.empty())
+        CKC(cudaMemcpy(h->dom_off, dom_off.data(), sizeof(int) * dom_off.size(), cudaMemcpyHostToDevice));
+    CKC(cudaMalloc(&h->dom_cell0, sizeof(int) * dom_cell0.size()));
+    CKC(cudaMemcpy(h->dom_cell0, dom_cell0.data(), sizeof(int) * dom_cell0.size(), cudaMemcpyHostToDevice));
+    if (h->mixed)
+        CKC(cudaFuncSetAttribute(k_ssa_domains<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SSA_DOMAIN_SMEM));
+    else
+        CKC(cudaFuncSetAttribute(k_ssa_domains<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, SSA_DOMAIN_SMEM));
     for (int m = 0; m < 2; ++m) {
         CKC(cudaMalloc(&h->col_cells[m], sizeof(int) * c1));
         if (!col_cells[m].empty())
@@ -748,6 +818,8 @@ int dpde_get_tuning(dpde_handle* h, dpde_tuning* out) {
     out->tile_edge = h->tile_edge;
     out->block = h->block;
     out->ssa_block = h->ssa_block;
+    out->ssa_mode = h->ssa_mode;
+    out->ssa_group = h->ssa_group > 0 ? h->ssa_group : h->dom_group_auto;
     out->reserved = 0;
     out->ms_per_step = 0.0;
     return DPDE_OK;
@@ -757,6 +829,7 @@ int dpde_set_tuning(dpde_handle* h, const dpde_tuning* t) {
     if (!h || !t) return DPDE_ERR_ARG;
     if (t->tile_edge < 2 || t->tile_edge > TILE_EDGE_MAX || t->block < 64 || t->block > 1024 ||
         t->block % 32 != 0 || t->ssa_block < 32 || t->ssa_block > SSA_THREADS_MAX || t->ssa_block % 32 != 0 ||
+        (t->ssa_mode != 0 && t->ssa_mode != 1) || t->ssa_group < 0 || t->ssa_group > SSA_GROUP_MAX ||
         t->reserved != 0)
         return fail(h, DPDE_ERR_ARG, "tuning out of range");
     CK(h, cudaStreamSynchronize(h->stream));
@@ -768,6 +841,8 @@ int dpde_set_tuning(dpde_handle* h, const dpde_tuning* t) {
     }
     h->block = t->block;
     h->ssa_block = t->ssa_block;
+    h->ssa_mode = t->ssa_mode;
+    h->ssa_group = t->ssa_group;
     return DPDE_OK;
 }
 
@@ -839,14 +914,20 @@ int dpde_autotune(dpde_handle* h, int32_t scheme, double dt, int32_t steps, dpde
         if (copy_all(true) != cudaSuccess) { rc = fail(h, DPDE_ERR_CUDA, "saving the state"); break; }
         double best_ms = 0.0;
         if ((rc = trial(best, best_ms)) != DPDE_OK) break;
-        const int edges[] = {4, 5, 6, 7, 8}, blocks[] = {128, 256, 512}, ssa_blocks[] = {32, 64, 128};
-        for (int stage = 0; stage < 3 && rc == DPDE_OK; ++stage) {
-            const int* cand = stage == 0 ? edges : (stage == 1 ? blocks : ssa_blocks);
-            const int nc = stage == 0 ? 5 : 3;
+        const int edges[] = {4, 5, 6, 7, 8}, blocks[] = {128, 256, 512}, ssa_blocks[] = {32, 64, 128},
+                  modes[] = {1, 0}, groups[] = {1, 2, 3, 4};
+        const int* cands[] = {edges, blocks, ssa_blocks, modes, groups};
+        const int ncands[] = {5, 3, 3, 2, 4};
+        for (int stage = 0; stage < 5 && rc == DPDE_OK; ++stage) {
+            // bricks per warp matter only to the per-brick SSA launch
+            if (stage == 4 && (best.ssa_mode != 1 || scheme != DPDE_HYBRID)) break;
+            const int* cand = cands[stage];
+            const int nc = ncands[stage];
             dpde_tuning base = best;
             for (int c = 0; c < nc && rc == DPDE_OK; ++c) {
                 dpde_tuning t = base;
-                (stage == 0 ? t.tile_edge : (stage == 1 ? t.block : t.ssa_block)) = cand[c];
+                int* field[] = {&t.tile_edge, &t.block, &t.ssa_block, &t.ssa_mode, &t.ssa_group};
+                *field[stage] = cand[c];
                 double ms = 0.0;
                 rc = trial(t, ms);
                 // a candidate must beat the incumbent by more than the trial noise

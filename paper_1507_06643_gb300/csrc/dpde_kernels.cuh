@@ -1008,26 +1008,42 @@ __device__ __forceinline__ double ssa_div(double x, double y) { return x / y; }
 __device__ __forceinline__ float ssa_beta(ff e, const RepInfo& R) { return __fdividef(R.cvf, e.hi); }
 __device__ __forceinline__ double ssa_beta(double e, const RepInfo& R) { return R.cv / e; }
 
+// Explicitly rounded operations: the compiler neither fuses nor reorders them,
+// so every kernel that inlines the pair map computes the same bits.
+__device__ __forceinline__ float r_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float r_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float r_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // k2 = 2 dt / m
 template <class T>
 __device__ __forceinline__ void ssa_pair_map(const Ctx<T>& C, const RepInfo& R, vec_t<T>& ps, eps_t<T>& es,
                                              T& bs, vec_t<T>& pt, eps_t<T>& et, const vec_t<T>& g, T k2,
                                              T amp0) {
     const T w = g.w;
-    const T chik = w * w * k2;
-    const T gam = C.sig2_4 * (bs + pt.w);
-    const T aa = gam * chik;   // a = 2 gamma chi dt / m
-    const T amp = (gam != T(0)) ? C.sigma * tsqrt(ssa_div(C.m * (-texpm1(T(-2) * aa)), gam)) : amp0 * w;
+    const T chik = r_mul(r_mul(w, w), k2);
+    const T gam = r_mul(C.sig2_4, r_add(bs, pt.w));
+    const T aa = r_mul(gam, chik);   // a = 2 gamma chi dt / m
+    const T amp = (gam != T(0)) ? r_mul(C.sigma, tsqrt(ssa_div(r_mul(C.m, -texpm1(T(-2) * aa)), gam)))
+                                : r_mul(amp0, w);
     const T em1 = texpm1(-aa);
-    const T Dx = T(0.5) * (em1 * (ps.x - pt.x) + amp * g.x);
-    const T Dy = T(0.5) * (em1 * (ps.y - pt.y) + amp * g.y);
-    const T Dz = T(0.5) * (em1 * (ps.z - pt.z) + amp * g.z);
-    const T snx = ps.x + Dx, sny = ps.y + Dy, snz = ps.z + Dz;
-    const T tnx = pt.x - Dx, tny = pt.y - Dy, tnz = pt.z - Dz;
+    const T Dx = r_mul(T(0.5), r_fma(em1, r_sub(ps.x, pt.x), r_mul(amp, g.x)));
+    const T Dy = r_mul(T(0.5), r_fma(em1, r_sub(ps.y, pt.y), r_mul(amp, g.y)));
+    const T Dz = r_mul(T(0.5), r_fma(em1, r_sub(ps.z, pt.z), r_mul(amp, g.z)));
+    const T snx = r_add(ps.x, Dx), sny = r_add(ps.y, Dy), snz = r_add(ps.z, Dz);
+    const T tnx = r_sub(pt.x, Dx), tny = r_sub(pt.y, Dy), tnz = r_sub(pt.z, Dz);
     // kinetic-energy change of the stored momenta, halved
-    const T dK = ((snx - ps.x) * (snx + ps.x) + (sny - ps.y) * (sny + ps.y) + (snz - ps.z) * (snz + ps.z) +
-                  (tnx - pt.x) * (tnx + pt.x) + (tny - pt.y) * (tny + pt.y) + (tnz - pt.z) * (tnz + pt.z)) *
-                 (T(0.25) * C.inv_m);
+    T q = r_mul(r_sub(tnz, pt.z), r_add(tnz, pt.z));
+    q = r_fma(r_sub(tny, pt.y), r_add(tny, pt.y), q);
+    q = r_fma(r_sub(tnx, pt.x), r_add(tnx, pt.x), q);
+    q = r_fma(r_sub(snz, ps.z), r_add(snz, ps.z), q);
+    q = r_fma(r_sub(sny, ps.y), r_add(sny, ps.y), q);
+    q = r_fma(r_sub(snx, ps.x), r_add(snx, ps.x), q);
+    const T dK = r_mul(q, r_mul(T(0.25), C.inv_m));
     ps.x = snx; ps.y = sny; ps.z = snz;
     es = eps_add(es, -dK);
     bs = ssa_beta(es, R);
@@ -1064,17 +1080,11 @@ __device__ void ssa_chain_plain(const Ctx<T>& C, const RepInfo& R, int b, int e,
 // dynamic shared memory of k_ssa_colour: two row tables [SSA_ROWS][block]
 __host__ __device__ constexpr size_t ssa_smem_bytes(int block) { return (size_t)2 * SSA_ROWS * block * sizeof(int); }
 
+// The chain of cell c on the calling thread (its column tid of the shared
+// row tables, bdim columns).
 template <class T>
-__global__ void __launch_bounds__(SSA_THREADS_MAX) k_ssa_colour(Ctx<T> C, const int* __restrict__ cells,
-                                                                int ncol, T dt, T sqrt_dt) {
-    extern __shared__ int ssa_rows[];
-    const int bdim = blockDim.x;
-    int* row_s = ssa_rows;                      // [r * bdim + tid]: slot of each non-empty row
-    int* row_n = ssa_rows + SSA_ROWS * bdim;    //                   its entry count
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= ncol) return;
-    const int tid = threadIdx.x;
-    const int c = cells[u];
+__device__ __forceinline__ void ssa_cell_chain(const Ctx<T>& C, int c, T dt, T sqrt_dt, int* row_s, int* row_n,
+                                               int bdim, int tid) {
     const int b = C.start[c], e = C.start[c + 1];
     int nrow = 0, total = 0;
     for (int s = b; s < e; ++s) {
@@ -1183,6 +1193,228 @@ __global__ void __launch_bounds__(SSA_THREADS_MAX) k_ssa_colour(Ctx<T> C, const 
     ps.w = bs;
     C.pB[s] = ps;
     C.eB[s] = es;
+}
+
+// One colour class: one thread per cell of the class.
+template <class T>
+__global__ void __launch_bounds__(SSA_THREADS_MAX) k_ssa_colour(Ctx<T> C, const int* __restrict__ cells,
+                                                                int ncol, T dt, T sqrt_dt) {
+    extern __shared__ int ssa_rows[];
+    const int bdim = blockDim.x;
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= ncol) return;
+    ssa_cell_chain(C, cells[u], dt, sqrt_dt, ssa_rows, ssa_rows + SSA_ROWS * bdim, bdim, (int)threadIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// The same SSA sequence domain by domain (Hybrid, Sec. III.B.2). The chains of
+// a domain never leave it, so two domains share no particle and their
+// sequences commute: each warp takes `group` consecutive domains (one slot
+// range, the cells being brick-major) and walks their colour classes in
+// order, its lanes running the chains of one class at a time (cells of one
+// class share no particle), with a warp barrier between classes (which also
+// orders the lanes' memory accesses). The result is the class-by-class
+// sequence bit for bit.
+//
+// The warp stages the state (p, eps) of its slot range in shared memory for
+// all its classes when it fits in `scap` slots, and otherwise works on the
+// state in place in global memory; in both cases a chain reads a state just
+// before the map that uses it, so no load can miss an earlier store. The
+// entries of a chain -- partner index and (G, w) -- are loaded SSA_AHEAD
+// entries ahead. `bcells` holds the cells of each domain sorted by class,
+// `boff[b * (NCOLOURS + 1) + k]` the start of class k of domain b and
+// `bcell0[b]` the first cell of domain b (bcell0[nbricks] = ncells).
+// ---------------------------------------------------------------------------
+constexpr int SSA_GROUP_MAX = 8;
+constexpr int SSA_AHEAD = 4;
+constexpr int SSA_DOMAIN_SMEM = 200 * 1024;   // dynamic shared memory of one k_ssa_domains block, at most
+
+// the particle state of a warp's slot range: staged (shared memory) or in place
+template <class T>
+struct SsaState {
+    vec_t<T>* p;
+    eps_t<T>* e;
+    int base, n;   // slots base .. base + n - 1
+};
+
+// one forward entry of a chain: owner s, partner t, (G, w)
+template <class T>
+struct SsaEntry {
+    int s, t;
+    vec_t<T> g;
+};
+
+// next entry of the chain over slots .. e - 1 at (s, m) of a row of nf
+// entries; false past the last
+__device__ __forceinline__ bool ssa_next(const int* __restrict__ fwd_n, int& s, int& m, int& nf, int e) {
+    if (m + 1 < nf) {
+        ++m;
+        return true;
+    }
+    for (++s; s < e; ++s) {
+        nf = __ldg(fwd_n + s);
+        if (nf > 0) {
+            m = 0;
+            return true;
+        }
+    }
+    return false;
+}
+
+template <class T>
+__device__ __forceinline__ bool ssa_fetch(const Ctx<T>& C, int& s, int& m, int& nf, int e, SsaEntry<T>& q) {
+    if (!ssa_next(C.fwd_n, s, m, nf, e)) return false;
+    q.s = s;
+    q.t = __ldg(C.fwd_j + (size_t)m * C.N + s);
+    q.g = C.fwd_g[(size_t)s * C.nbr_cap + m];
+    return true;
+}
+
+// The chain of cell c on the state S. Entries are fetched in blocks of
+// SSA_AHEAD into two register sets used in turn (the loop is unrolled over
+// the pair, so no register is moved while its load is in flight): the loads
+// of block i + 1 are issued before the maps of block i run.
+template <class T>
+__device__ __forceinline__ void ssa_domain_chain(const Ctx<T>& C, const RepInfo& R, int c, const SsaState<T>& S,
+                                                 T k2, T amp0) {
+    int s = C.start[c] - 1, m = 0, nf = 0;
+    const int e = C.start[c + 1];
+    int cur = -1;
+    vec_t<T> ps;
+    eps_t<T> es;
+    T bs = T(0);
+    bool bad = false;
+    auto fill = [&](SsaEntry<T>(&q)[SSA_AHEAD], bool(&v)[SSA_AHEAD]) {
+        bool more = true;
+#pragma unroll
+        for (int a = 0; a < SSA_AHEAD; ++a) {
+            more = more && ssa_fetch(C, s, m, nf, e, q[a]);
+            v[a] = more;
+        }
+    };
+    auto run = [&](const SsaEntry<T>(&q)[SSA_AHEAD], const bool(&v)[SSA_AHEAD]) {
+#pragma unroll
+        for (int a = 0; a < SSA_AHEAD; ++a) {
+            if (!v[a]) break;
+            const SsaEntry<T>& x = q[a];
+            const int ls = x.s - S.base, lt = x.t - S.base;
+            if ((unsigned)ls >= (unsigned)S.n || (unsigned)lt >= (unsigned)S.n) {
+                bad = true;   // a chain left its domain: never by construction
+                break;
+            }
+            if (x.s != cur) {
+                if (cur >= 0) {
+                    ps.w = bs;
+                    S.p[cur - S.base] = ps;
+                    S.e[cur - S.base] = es;
+                }
+                cur = x.s;
+                ps = S.p[ls];
+                es = S.e[ls];
+                bs = ps.w;
+            }
+            vec_t<T> pt = S.p[lt];
+            eps_t<T> et = S.e[lt];
+            ssa_pair_map(C, R, ps, es, bs, pt, et, x.g, k2, amp0);
+            S.p[lt] = pt;
+            S.e[lt] = et;
+        }
+    };
+    SsaEntry<T> qa[SSA_AHEAD], qb[SSA_AHEAD];
+    bool va[SSA_AHEAD], vb[SSA_AHEAD];
+    fill(qa, va);
+    while (va[0] && !bad) {
+        fill(qb, vb);
+        run(qa, va);
+        if (!vb[0] || bad) break;
+        fill(qa, va);
+        run(qb, vb);
+    }
+    if (bad) {
+        flag(C.status, ST_DOMAIN);
+        return;
+    }
+    if (cur >= 0) {
+        ps.w = bs;
+        S.p[cur - S.base] = ps;
+        S.e[cur - S.base] = es;
+    }
+}
+
+// the colour classes of a warp's domains, in order, on the state S
+template <class T>
+__device__ __forceinline__ void ssa_domain_classes(const Ctx<T>& C, const int* __restrict__ bcells, const int* wo,
+                                                   int nb, const SsaState<T>& S, T k2, T amp0) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < NCOLOURS; ++k) {
+        int total = 0;
+        for (int g = 0; g < nb; ++g) total += wo[g * (NCOLOURS + 1) + k + 1] - wo[g * (NCOLOURS + 1) + k];
+        if (total == 0) continue;   // whole warp
+        for (int i = lane; i < total; i += 32) {
+            int g = 0, r = i;
+            for (;;) {
+                const int cnt = wo[g * (NCOLOURS + 1) + k + 1] - wo[g * (NCOLOURS + 1) + k];
+                if (r < cnt) break;
+                r -= cnt;
+                ++g;
+            }
+            const int c = bcells[wo[g * (NCOLOURS + 1) + k] + r];
+            ssa_domain_chain(C, C.reps[C.rep_of_cell[c]], c, S, k2, amp0);
+        }
+        __syncwarp();
+    }
+}
+
+// shared memory of one warp of k_ssa_domains: staged p and eps for scap
+// slots, then the class starts of `group` domains
+template <class T>
+__host__ __device__ constexpr size_t ssa_domain_warp_bytes(int group, int scap) {
+    return (size_t)scap * (sizeof(vec_t<T>) + sizeof(eps_t<T>)) +
+           (((size_t)group * (NCOLOURS + 1) * sizeof(int) + 15) / 16) * 16;
+}
+
+template <class T>
+__global__ void __launch_bounds__(SSA_THREADS_MAX) k_ssa_domains(Ctx<T> C, const int* __restrict__ bcells,
+                                                                 const int* __restrict__ boff,
+                                                                 const int* __restrict__ bcell0, int nbricks,
+                                                                 int group, int scap, T dt, T sqrt_dt) {
+    extern __shared__ __align__(16) unsigned char ssa_dom_smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int b0 = (int)((blockIdx.x * (blockDim.x >> 5) + wib) * group);
+    if (b0 >= nbricks) return;   // whole warp
+    const int nb = min(group, nbricks - b0);
+    unsigned char* wbase = ssa_dom_smem + (size_t)wib * ssa_domain_warp_bytes<T>(group, scap);
+    int* wo = reinterpret_cast<int*>(wbase + (size_t)scap * (sizeof(vec_t<T>) + sizeof(eps_t<T>)));
+    for (int i = lane; i < nb * (NCOLOURS + 1); i += 32) wo[i] = boff[(size_t)b0 * (NCOLOURS + 1) + i];
+    const int sb = C.start[bcell0[b0]], se = C.start[bcell0[b0 + nb]];
+    const T amp0 = T(2) * C.sigma * sqrt_dt;   // amplitude of the map as gamma -> 0
+    const T k2 = T(2) * dt * C.inv_m;
+    SsaState<T> S;
+    S.base = sb;
+    S.n = se - sb;
+    if (S.n <= scap) {   // whole warp
+        vec_t<T>* sp = reinterpret_cast<vec_t<T>*>(wbase);
+        eps_t<T>* se_ = reinterpret_cast<eps_t<T>*>(wbase + (size_t)scap * sizeof(vec_t<T>));
+        for (int i = lane; i < S.n; i += 32) {
+            sp[i] = C.pB[sb + i];
+            se_[i] = C.eB[sb + i];
+        }
+        __syncwarp();
+        S.p = sp;
+        S.e = se_;
+        ssa_domain_classes(C, bcells, wo, nb, S, k2, amp0);
+        __syncwarp();
+        for (int i = lane; i < S.n; i += 32) {
+            C.pB[sb + i] = sp[i];
+            C.eB[sb + i] = se_[i];
+        }
+    } else {
+        __syncwarp();
+        S.p = C.pB + sb;
+        S.e = C.eB + sb;
+        ssa_domain_classes(C, bcells, wo, nb, S, k2, amp0);
+    }
 }
 
 template <class T>

@@ -62,7 +62,8 @@ class dpde_obs(C.Structure):
 
 class dpde_tuning(C.Structure):
     _fields_ = [("tile_edge", C.c_int32), ("block", C.c_int32), ("ssa_block", C.c_int32),
-                ("reserved", C.c_int32), ("ms_per_step", C.c_double)]
+                ("ssa_mode", C.c_int32), ("ssa_group", C.c_int32), ("reserved", C.c_int32),
+                ("ms_per_step", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -194,7 +195,7 @@ def dpde_get_tuning(h) -> dict:
     return t.as_dict()
 
 
-def dpde_set_tuning(h, tile_edge=None, block=None, ssa_block=None):
+def dpde_set_tuning(h, tile_edge=None, block=None, ssa_block=None, ssa_mode=None, ssa_group=None):
     t = dpde_tuning()
     _check(h, lib().dpde_get_tuning(h, C.byref(t)))
     if tile_edge is not None:
@@ -203,6 +204,10 @@ def dpde_set_tuning(h, tile_edge=None, block=None, ssa_block=None):
         t.block = int(block)
     if ssa_block is not None:
         t.ssa_block = int(ssa_block)
+    if ssa_mode is not None:
+        t.ssa_mode = int(ssa_mode)
+    if ssa_group is not None:
+        t.ssa_group = int(ssa_group)
     _check(h, lib().dpde_set_tuning(h, C.byref(t)))
 
 

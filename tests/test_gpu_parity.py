@@ -288,9 +288,14 @@ def test_ssa_launches_follow_colour_classes(box, bricks):
             out *= min(P, k) + (k % P if periodic and k >= P else 0)
         return out
 
+    S.set_tuning(ssa_mode=0)
     ser, hyb, ssa = (S.step_launches(x) for x in ("SER", "HYBRID", "SSA"))
     assert hyb - ser == classes(False) + 1     # + the Gaussian pass
     assert ssa - (ser - 1) == classes(True) + 1   # SSA: one copy-back in place of the two sweeps
+    # per-domain form: one launch for every class of every domain; DPDE_SSA unchanged
+    S.set_tuning(ssa_mode=1)
+    assert S.step_launches("HYBRID") - ser == 2
+    assert S.step_launches("SSA") == ssa
     S.close()
 
 
@@ -436,6 +441,43 @@ def test_block_sizes_do_not_change_results(precision):
             assert np.array_equal(a, b), t
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("scheme", ["HYBRID", "SSA"])
+def test_ssa_modes_agree_bit_for_bit(precision, scheme):
+    # the per-domain launch (mode 1) and the per-class launches (mode 0) apply the same sequence
+    ref = _run_tuned(precision, {"ssa_mode": 0}, scheme=scheme)
+    for t in ({"ssa_mode": 1}, {"ssa_mode": 1, "ssa_block": 32}, {"ssa_mode": 1, "ssa_block": 128},
+              {"ssa_mode": 1, "ssa_group": 1}, {"ssa_mode": 1, "ssa_group": 3},
+              {"ssa_mode": 1, "ssa_group": 8, "ssa_block": 96}):
+        got = _run_tuned(precision, t, scheme=scheme)
+        for a, b in zip(ref, got):
+            assert np.array_equal(a, b), t
+
+
+@pytest.mark.parametrize("scheme", ["HYBRID", "SSA"])
+def test_ssa_modes_agree_on_thin_and_batched_boxes(scheme):
+    # three cells along an axis (the +2 and -1 offsets name the same cell), bricks two cells
+    # thick, and replicas of different sizes in one launch
+    from paper_1507_06643_gb300 import dpde
+    specs = [(1200, (3.2, 3.2, 38.0), 60.0, 1.0, (1, 1, 4)),
+             (900, (cube(900),) * 3, 40.0, 1.0, (2, 1, 3)),
+             (2000, (4.1, 9.0, 16.5), 80.0, 1.0, (1, 3, 1))]
+    q, p, e = make_state(specs, 91, True)
+    outs = []
+    for mode, group in ((0, 0), (1, 0), (1, 2), (1, 5)):
+        S = dpde.System(dpde.make_params(precision="mixed"),
+                        [dpde.make_replica(n, box, cv, br) for n, box, cv, _, br in specs])
+        S.set_tuning(ssa_mode=mode, ssa_group=group)
+        S.set_state(q, p, e)
+        S.step(4, 0.01, scheme)
+        outs.append(S.get_state())
+        assert S.tuning()["ssa_mode"] == mode
+        S.close()
+    for out in outs[1:]:
+        for a, b in zip(outs[0], out):
+            assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("edge", [2, 4, 5, 8])
 def test_tile_edge_changes_rounding_only(edge):
     ref = _run_tuned("fp64", None)
@@ -455,7 +497,8 @@ def test_autotune_keeps_the_state():
     step0 = dpde.dpde_get_step(S.h)
     t = S.autotune("HYBRID", 0.01, 2)
     assert t["tile_edge"] in (4, 5, 6, 7, 8) and t["block"] in (128, 256, 512)
-    assert t["ssa_block"] in (32, 64, 128) and t["ms_per_step"] > 0
+    assert t["ssa_block"] in (32, 64, 128) and t["ssa_mode"] in (0, 1) and t["ms_per_step"] > 0
+    assert 1 <= t["ssa_group"] <= 8
     assert S.tuning()["tile_edge"] == t["tile_edge"]
     after = S.get_state()
     for a, b in zip(before, after):
@@ -480,7 +523,7 @@ def test_bad_tuning_rejected():
     from paper_1507_06643_gb300 import dpde
     S = dpde.System(dpde.make_params(precision="mixed"), [dpde.make_replica(300, (cube(300),) * 3, 50.0)])
     for kw in ({"tile_edge": 1}, {"tile_edge": 9}, {"block": 48}, {"block": 2048}, {"ssa_block": 256},
-               {"ssa_block": 48}):
+               {"ssa_block": 48}, {"ssa_mode": 2}, {"ssa_mode": -1}, {"ssa_group": 9}, {"ssa_group": -1}):
         with pytest.raises(dpde.DPDEError):
             S.set_tuning(**kw)
     S.close()
