@@ -127,7 +127,7 @@ KERNEL_OF_PHASE = {"ssa": "k_ssa_colour", "ssa_gauss": "k_ssa_gauss", "sweep1": 
 # named configuration with the caches kept warm
 # (profiles/launches_large_n4m_hybrid_mixed.md); reported only for that
 # configuration and kernel.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {("large_n4m", "HYBRID", "mixed", "k_ssa_colour"): 168.6e6}
 
 
 def pair_counts(w):

@@ -357,13 +357,13 @@ typedef struct dpde_tuning {
                          /* of 32 in 64..1024 (default 256)                           */
     int32_t ssa_block;   /* threads per block of the SSA launches: 32, 64, 96 or 128   */
                          /* (default 64)                                               */
-    int32_t ssa_mode;    /* 0 (default): one SSA launch per colour class; 1: the Hybrid */
-                         /* SSA sequence as one launch in which each warp takes whole  */
-                         /* domains and walks their colour classes in order (domains   */
-                         /* share no chain, so their sequences commute), with the      */
-                         /* domains' state staged in shared memory where it fits. Both */
-                         /* give the same results bit for bit. DPDE_SSA always takes   */
-                         /* the per-class launches (its chains span the replica).      */
+    int32_t ssa_mode;    /* form of the SSA launches; both give the same results bit  */
+                         /* for bit. 0 (default): one launch per colour class, a      */
+                         /* thread per cell; 1 (Hybrid only, DPDE_SSA then takes 0):  */
+                         /* one launch in which each warp takes whole domains and     */
+                         /* walks their colour classes in order (domains share no     */
+                         /* chain, so their sequences commute), the domains' state    */
+                         /* staged in shared memory where it fits                     */
     int32_t ssa_group;   /* domains per warp of ssa_mode 1, 1..8; 0 = automatic (32 /  */
                          /* the most cells of one class in one domain); get_tuning     */
                          /* reports the value in use                                   */

@@ -1001,11 +1001,15 @@ __global__ void k_ssa_gauss(Ctx<T> C) {
 // The pair map on (p_s, eps_s, beta_s) in registers and partner (p_t, eps_t)
 // with beta_t = p_t.w, for the entry (G, w) = g; returns the new partner
 // state, beta in .w.
-// x / y: exact in double; in float through the fast reciprocal (2 ulp), which
-// keeps the chains' critical path short
-__device__ __forceinline__ float ssa_div(float x, float y) { return __fdividef(x, y); }
-__device__ __forceinline__ double ssa_div(double x, double y) { return x / y; }
+// beta = C_v / eps: exact in double; in float through the fast reciprocal
+// (2 ulp), which keeps the chains' critical path short
 __device__ __forceinline__ float ssa_beta(ff e, const RepInfo& R) { return __fdividef(R.cvf, e.hi); }
+// sqrt(x / y) for x >= 0, y > 0: exact in double; in float x rsqrt(x y) (a
+// few ulp, for x y a normal float; 0 for x = 0)
+__device__ __forceinline__ float ssa_sqrt_ratio(float x, float y) {
+    return x > 0.0f ? __fmul_rn(x, rsqrtf(__fmul_rn(x, y))) : 0.0f;
+}
+__device__ __forceinline__ double ssa_sqrt_ratio(double x, double y) { return sqrt(x / y); }
 __device__ __forceinline__ double ssa_beta(double e, const RepInfo& R) { return R.cv / e; }
 
 // Explicitly rounded operations: the compiler neither fuses nor reorders them,
@@ -1028,9 +1032,10 @@ __device__ __forceinline__ void ssa_pair_map(const Ctx<T>& C, const RepInfo& R, 
     const T chik = r_mul(r_mul(w, w), k2);
     const T gam = r_mul(C.sig2_4, r_add(bs, pt.w));
     const T aa = r_mul(gam, chik);   // a = 2 gamma chi dt / m
-    const T amp = (gam != T(0)) ? r_mul(C.sigma, tsqrt(ssa_div(r_mul(C.m, -texpm1(T(-2) * aa)), gam)))
-                                : r_mul(amp0, w);
+    // e^{-a} - 1, and 1 - e^{-2a} = -(e^{-a} - 1)(e^{-a} - 1 + 2)
     const T em1 = texpm1(-aa);
+    const T x = r_mul(C.m, -r_mul(em1, r_add(em1, T(2))));   // m (1 - e^{-2a})
+    const T amp = (gam != T(0)) ? r_mul(C.sigma, ssa_sqrt_ratio(x, gam)) : r_mul(amp0, w);
     const T Dx = r_mul(T(0.5), r_fma(em1, r_sub(ps.x, pt.x), r_mul(amp, g.x)));
     const T Dy = r_mul(T(0.5), r_fma(em1, r_sub(ps.y, pt.y), r_mul(amp, g.y)));
     const T Dz = r_mul(T(0.5), r_fma(em1, r_sub(ps.z, pt.z), r_mul(amp, g.z)));
