@@ -118,7 +118,7 @@ def workload_and_scheme(args):
 # SSA pair map ~130 (2 expm1, 1 div, 1 sqrt, momenta, dK, two compensated eps
 # updates, two beta divisions); SER sweep 1 ~40, sweep 2 ~55 pair arithmetic.
 OPS_GAUSS = 180.0
-OPS_PER_PAIR = {"ssa": 130.0, "ssa_gauss": OPS_GAUSS, "sweep1": OPS_GAUSS + 40.0, "sweep2": OPS_GAUSS + 55.0}
+OPS_PER_PAIR = {"ssa": 95.0, "ssa_gauss": OPS_GAUSS, "sweep1": OPS_GAUSS + 40.0, "sweep2": OPS_GAUSS + 55.0}
 KERNEL_OF_PHASE = {"ssa": "k_ssa_colour", "ssa_gauss": "k_ssa_gauss", "sweep1": "k_ser_sweep1",
                    "sweep2": "k_ser_sweep2", "force": "k_force_tile", "gather": "k_rank_gather",
                    "kick_drift": "k_kick_drift_key"}
