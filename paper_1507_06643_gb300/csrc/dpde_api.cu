@@ -287,7 +287,9 @@ void enqueue_set_state(dpde_handle* h, cudaStream_t st, const double* q, const d
 template <class T>
 void enqueue_get_state(dpde_handle* h, cudaStream_t st, double* q, double* p, double* e) {
     const Ctx<T> C = make_ctx<T>(h);
-    k_get_state<T><<<ceil_div(h->N, h->block), h->block, 0, st>>>(C, q, p, e);
+    // the sort's scratch (tmp, N ints) holds the id -> slot map between steps
+    k_slot_of_id<T><<<ceil_div(h->N, h->block), h->block, 0, st>>>(C, h->tmp);
+    k_get_state<T><<<ceil_div(h->N, h->block), h->block, 0, st>>>(C, h->tmp, q, p, e);
 }
 
 template <class T>

@@ -156,8 +156,10 @@ __global__ void k_load_state(Ctx<T> C, const double* __restrict__ q, const doubl
     T o[3];
     for (int d = 0; d < 3; ++d) {
         double x = q[3 * s + d];
-        x -= R.L[d] * floor(x / R.L[d]);
-        if (x >= R.L[d]) x -= R.L[d];
+        if (!(x >= 0.0 && x < R.L[d])) {   // wrap only what lies outside [0, L) (FP64 division is slow)
+            x -= R.L[d] * floor(x / R.L[d]);
+            if (x >= R.L[d]) x -= R.L[d];
+        }
         int cd = (int)(x * R.s[d]);
         cd = cd > R.nc[d] - 1 ? R.nc[d] - 1 : (cd < 0 ? 0 : cd);
         c[d] = cd;
@@ -175,27 +177,39 @@ __global__ void k_load_state(Ctx<T> C, const double* __restrict__ q, const doubl
     C.cA[s] = pack_cell(c[0], c[1], c[2]);
 }
 
+// slot of every particle of set A, by global id (part_off + id)
 template <class T>
-__global__ void k_get_state(Ctx<T> C, double* __restrict__ q, double* __restrict__ p,
-                            double* __restrict__ e) {
+__global__ void k_slot_of_id(Ctx<T> C, int* __restrict__ slot_of) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= C.N) return;
+    slot_of[C.reps[C.rep_of_slot[s]].part_off + (int)id_of(C.qA[s])] = s;
+}
+
+// the state of set A in id order: one thread per id gathers its slot, so the
+// FP64 outputs are written contiguously
+template <class T>
+__global__ void k_get_state(Ctx<T> C, const int* __restrict__ slot_of, double* __restrict__ q,
+                            double* __restrict__ p, double* __restrict__ e) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= C.N) return;
+    const int s = slot_of[g];
     const RepInfo& R = C.reps[C.rep_of_slot[s]];
-    const vec_t<T> qv = C.qA[s];
-    const vec_t<T> pv = C.pA[s];
-    const int cc = C.cA[s];
-    const long long g = (long long)R.part_off + id_of(qv);
     if (q) {
+        const vec_t<T> qv = C.qA[s];
+        const int cc = C.cA[s];
         const int cd[3] = {cell_x(cc), cell_y(cc), cell_z(cc)};
         const double od[3] = {(double)qv.x, (double)qv.y, (double)qv.z};
         for (int d = 0; d < 3; ++d) {
             double x = (double)cd[d] * R.ell[d] + od[d];
             if (x >= R.L[d]) x -= R.L[d];
             else if (x < 0.0) x += R.L[d];
-            q[3 * g + d] = x;
+            q[3 * (size_t)g + d] = x;
         }
     }
-    if (p) { p[3 * g] = (double)pv.x; p[3 * g + 1] = (double)pv.y; p[3 * g + 2] = (double)pv.z; }
+    if (p) {
+        const vec_t<T> pv = C.pA[s];
+        p[3 * (size_t)g] = (double)pv.x; p[3 * (size_t)g + 1] = (double)pv.y; p[3 * (size_t)g + 2] = (double)pv.z;
+    }
     if (e) e[g] = eps_value(C.eA[s]);
 }
 
