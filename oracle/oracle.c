@@ -87,7 +87,11 @@ void ora_gaussian_batch(int64_t n, uint64_t seed, const uint32_t* step,
 /* Geometry                                                                  */
 /* ------------------------------------------------------------------------ */
 
-/* Minimum-image vector q_i - q_j and its squared length. */
+/* Whether axis d of a replica is periodic (z is not between walls). */
+static int periodic_axis(const ora_replica* rep, int d) { return !(d == 2 && rep->walls); }
+
+/* Minimum-image vector q_i - q_j (plain difference along a walled axis) and
+ * its squared length. */
 static double min_image(const ora_replica* rep, const double* q, int64_t i, int64_t j,
                         double dx[3])
 {
@@ -95,7 +99,7 @@ static double min_image(const ora_replica* rep, const double* q, int64_t i, int6
     for (int d = 0; d < 3; ++d) {
         double L = rep->box[d];
         double x = q[3 * i + d] - q[3 * j + d];
-        x -= L * round(x / L);
+        if (periodic_axis(rep, d)) x -= L * round(x / L);
         dx[d] = x;
         r2 += x * x;
     }
@@ -189,6 +193,7 @@ int64_t ora_pairs_cells(const ora_replica* rep, double r_cut, const double* q, i
         for (int dz = -1; dz <= 1; ++dz)
             for (int dy = -1; dy <= 1; ++dy)
                 for (int ddx = -1; ddx <= 1; ++ddx) {
+                    if (!periodic_axis(rep, 2) && (ci[2] + dz < 0 || ci[2] + dz >= cl.nc[2])) continue;
                     int cx = (ci[0] + ddx + cl.nc[0]) % cl.nc[0];
                     int cy = (ci[1] + dy + cl.nc[1]) % cl.nc[1];
                     int cz = (ci[2] + dz + cl.nc[2]) % cl.nc[2];
@@ -443,9 +448,9 @@ static void ssa_pair(const fd_ctx* c, int64_t i, int64_t j)
 /* Colour of a cell coordinate l along one axis of a domain with k cells and
  * colour period P (3 along x and y, 2 along z -- the forward half stencil
  * spans offsets -1..1 along x and y but only 0..1 along z): l mod P, except
- * that along a periodic domain axis (one domain spanning the replica) the
- * trailing k mod P cells take colours P, P + 1, so that two cells of equal
- * colour are at least P cells apart around the ring. */
+ * that along a periodic domain axis (one domain spanning a periodic axis of
+ * the replica) the trailing k mod P cells take colours P, P + 1, so that two
+ * cells of equal colour are at least P cells apart around the ring. */
 static int axis_colour(int l, int k, int P, int periodic)
 {
     int full = P * (k / P);
@@ -488,7 +493,8 @@ static int ssa_sequence(const ora_replica* rep, double r_cut, const double* q, i
                             for (int d = 0; d < 3; ++d) {
                                 loc[d] = cc[d] % k[d];
                                 brick[d] = cc[d] / k[d];
-                                if (axis_colour(loc[d], k[d], period[d], B[d] == 1) != kcol[d]) match = 0;
+                                const int ring = B[d] == 1 && periodic_axis(rep, d);
+                                if (axis_colour(loc[d], k[d], period[d], ring) != kcol[d]) match = 0;
                             }
                             if (!match) continue;
                             int64_t c0 = ((int64_t)cz * cl.nc[1] + cy) * cl.nc[0] + cx;
@@ -499,7 +505,7 @@ static int ssa_sequence(const ora_replica* rep, double r_cut, const double* q, i
                                     int nb[3], valid = 1;
                                     for (int d = 0; d < 3; ++d) {
                                         int ln = loc[d] + del[d];
-                                        if (B[d] == 1) ln = (ln + k[d]) % k[d];
+                                        if (B[d] == 1 && periodic_axis(rep, d)) ln = (ln + k[d]) % k[d];
                                         else if (ln < 0 || ln >= k[d]) valid = 0;
                                         nb[d] = brick[d] * k[d] + ln;
                                     }
@@ -594,14 +600,30 @@ int ora_fd(const ora_replica* rep, int32_t ridx, const ora_params* prm, const do
 /* Full step: velocity Verlet, then the fluctuation/dissipation scheme       */
 /* ------------------------------------------------------------------------ */
 
-static void wrap_positions(const ora_replica* rep, double* q)
+/* After the drift of step `step` (0-based): periodic wrap, or along a walled
+ * z axis the specular reflections at z = 0 and at z_w = L_z + u (step + 1) dt
+ * (z -> 2 z_w - z, p_z -> 2 m u - p_z). */
+static void wrap_positions(const ora_replica* rep, const ora_params* prm, double* q, double* p,
+                           int64_t step, double dt)
 {
+    const double zw = rep->box[2] + rep->wall_u * (double)(step + 1) * dt;
     for (int64_t i = 0; i < rep->n; ++i)
         for (int d = 0; d < 3; ++d) {
             double L = rep->box[d];
             double x = q[3 * i + d];
-            if (x >= L) x -= L;
-            else if (x < 0.0) x += L;
+            if (!periodic_axis(rep, d)) {
+                if (x < 0.0) {
+                    x = -x;
+                    p[3 * i + d] = -p[3 * i + d];
+                } else if (x > zw) {
+                    x = 2.0 * zw - x;
+                    p[3 * i + d] = 2.0 * prm->mass * rep->wall_u - p[3 * i + d];
+                }
+            } else if (x >= L) {
+                x -= L;
+            } else if (x < 0.0) {
+                x += L;
+            }
             q[3 * i + d] = x;
         }
 }
@@ -612,8 +634,11 @@ int ora_run(int32_t n_rep, const ora_replica* reps, const ora_params* prm, doubl
 {
     if (n_rep < 1 || scheme < 0 || scheme > 3 || !(dt > 0.0)) return -1;
     int32_t nc[3], k[3];
-    for (int r = 0; r < n_rep; ++r)
+    for (int r = 0; r < n_rep; ++r) {
         if (ora_cell_grid(&reps[r], prm->r_cut, nc, k) != 0) return -1;
+        if (reps[r].walls != 0 && reps[r].walls != 1) return -1;
+        if (reps[r].walls && !(reps[r].wall_u <= 0.0)) return -1;
+    }
     for (int64_t s = 0; s < nsteps; ++s) {
         int64_t off = 0;
         for (int r = 0; r < n_rep; ++r) {
@@ -625,7 +650,7 @@ int ora_run(int32_t n_rep, const ora_replica* reps, const ora_params* prm, doubl
             int64_t n = rep->n;
             for (int64_t i = 0; i < 3 * n; ++i) pr[i] += 0.5 * dt * Fr[i];
             for (int64_t i = 0; i < 3 * n; ++i) qr[i] += dt * pr[i] / prm->mass;
-            wrap_positions(rep, qr);
+            wrap_positions(rep, prm, qr, pr, step0 + s, dt);
             if (ora_forces(rep, prm, qr, Fr) != 0) return -1;
             for (int64_t i = 0; i < 3 * n; ++i) pr[i] += 0.5 * dt * Fr[i];
             if (ora_fd(rep, r, prm, qr, pr, er, (uint32_t)(step0 + s), dt, scheme) != 0) return -1;

@@ -40,12 +40,20 @@ enum { ORA_POT_SOFT = 0, ORA_POT_LJ = 1 };
 /* v(r), v'(r), v''(r) of the pair potential (r < r_cut). */
 void ora_pair_potential(const ora_params* prm, double r, double* v, double* dv, double* d2v);
 
+/* A replica is periodic along x and y; along z it is periodic (walls = 0)
+ * or closed by two specular walls (walls = 1): a fixed wall at z = 0 and a
+ * wall at z_w(n) = L_z + wall_u n dt after step n (wall_u <= 0, a piston).
+ * A particle that crosses a wall during the drift is reflected:
+ * z -> 2 z_w - z, p_z -> 2 m u_w - p_z (u_w = 0 for the fixed wall), and no
+ * pair interacts across the z boundary. This is the hard-wall reading of the
+ * confining walls of the shock set-up (Sec. V). */
 typedef struct ora_replica {
     int64_t n;
     double  box[3];
     double  cv;
     int32_t bricks[3];
-    int32_t reserved;
+    int32_t walls;
+    double  wall_u;
 } ora_replica;
 
 enum { ORA_SER = 0, ORA_HYBRID = 1, ORA_SEM = 2, ORA_SSA = 3 };

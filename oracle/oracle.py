@@ -48,7 +48,7 @@ POT_SOFT, POT_LJ = 0, 1
 
 class Replica(C.Structure):
     _fields_ = [("n", C.c_int64), ("box", C.c_double * 3), ("cv", C.c_double),
-                ("bricks", C.c_int32 * 3), ("reserved", C.c_int32)]
+                ("bricks", C.c_int32 * 3), ("walls", C.c_int32), ("wall_u", C.c_double)]
 
 
 _lib = None
@@ -105,7 +105,8 @@ def pair_potential(prm: Params, r: float):
     return v.value, dv.value, d2v.value
 
 
-def make_replica(n, box, cv, bricks=(1, 1, 1)) -> Replica:
+def make_replica(n, box, cv, bricks=(1, 1, 1), walls=0, wall_u=0.0) -> Replica:
+    """walls = 1: specular walls at z = 0 and z = L_z + wall_u n dt (oracle.h)."""
     if np.isscalar(box):
         box = (box, box, box)
     r = Replica()
@@ -113,7 +114,8 @@ def make_replica(n, box, cv, bricks=(1, 1, 1)) -> Replica:
     r.box[:] = [float(x) for x in box]
     r.cv = float(cv)
     r.bricks[:] = [int(b) for b in bricks]
-    r.reserved = 0
+    r.walls = int(walls)
+    r.wall_u = float(wall_u)
     return r
 
 
