@@ -176,7 +176,7 @@ def run_ours(args):
     if world > 1:
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = workload_and_scheme(args)
-    spec_reps = [dpde.make_replica(s.n, s.box, s.cv, s.bricks) for s in w.replicas]
+    spec_reps = [dpde.make_replica(s.n, s.box, s.cv, s.bricks, s.walls, s.wall_u) for s in w.replicas]
     prm = dpde.make_params(w.mass, w.r_cut, w.a, w.sigma, w.seed + 7919 * rank, w.precision)
     q, p, e = inputs.workload_state(w, seed=w.seed + rank)
     stream = torch.cuda.Stream()
@@ -342,7 +342,7 @@ def drift_run(args, stream):
     every = max(1, min(1000, args.drift_steps // 10))
     for prec in ("mixed", "fp64"):
         w = inputs.equilibrium_n108000(prec)
-        reps = [dpde.make_replica(x.n, x.box, x.cv, x.bricks) for x in w.replicas]
+        reps = [dpde.make_replica(x.n, x.box, x.cv, x.bricks, x.walls, x.wall_u) for x in w.replicas]
         S = dpde.System(dpde.make_params(w.mass, w.r_cut, w.a, w.sigma, w.seed, prec), reps,
                         stream=stream.cuda_stream)
         q, p, e = inputs.workload_state(w)
@@ -390,7 +390,9 @@ def oracle_sample(w, n_target: int):
     b = max(1, int(L // cells_per_brick)) if spec.bricks != (1, 1, 1) else 1
     while b > 1 and math.floor(L / b) * b < 3:
         b -= 1
-    sub = inputs.Workload(w.name + "_sample", [inputs.ReplicaSpec(n, (L, L, L), spec.cv, spec.kT, (b, b, b))],
+    sub = inputs.Workload(w.name + "_sample", [inputs.ReplicaSpec(n, (L, L, L), spec.cv, spec.kT, (b, b, b),
+                                                                  spec.vz_split, spec.vz_shift, spec.walls,
+                                                                  spec.wall_u)],
                           w.mass, w.r_cut, w.a, w.sigma, w.dt, 1, w.seed, "fp64")
     return sub
 
@@ -403,7 +405,7 @@ def cpu_baseline(w, scheme: str, seconds: float, steps: int | None = None):
     sub = oracle_sample(w, n_target)
     spec = sub.replicas[0]
     q, p, e = inputs.workload_state(sub, float32=False)
-    S = O.System([O.make_replica(spec.n, spec.box, spec.cv, spec.bricks)],
+    S = O.System([O.make_replica(spec.n, spec.box, spec.cv, spec.bricks, spec.walls, spec.wall_u)],
                  O.make_params(sub.mass, sub.r_cut, sub.a, sub.sigma, sub.seed), q, p, e)
     nsteps = steps or 1
     t = time.perf_counter()
@@ -426,7 +428,7 @@ def _gpu_vs_oracle(sub, q, p, e, ref, nsteps, scheme, precision):
     from paper_1507_06643_gb300 import dpde
     spec = sub.replicas[0]
     G = dpde.System(dpde.make_params(sub.mass, sub.r_cut, sub.a, sub.sigma, sub.seed, precision),
-                    [dpde.make_replica(spec.n, spec.box, spec.cv, spec.bricks)])
+                    [dpde.make_replica(spec.n, spec.box, spec.cv, spec.bricks, spec.walls, spec.wall_u)])
     G.set_state(q, p, e)
     G.step(nsteps, sub.dt, scheme, use_graph=False)
     qg, pg, eg = G.get_state()
@@ -451,7 +453,7 @@ def parity_report(w, base, scheme):
     small = oracle_sample(w, 60000)
     spec = small.replicas[0]
     q2, p2, e2 = inputs.workload_state(small, float32=True)
-    ref2 = O.System([O.make_replica(spec.n, spec.box, spec.cv, spec.bricks)],
+    ref2 = O.System([O.make_replica(spec.n, spec.box, spec.cv, spec.bricks, spec.walls, spec.wall_u)],
                     O.make_params(small.mass, small.r_cut, small.a, small.sigma, small.seed), q2, p2, e2)
     ref2.run(2, small.dt, "SER")
     out["mixed_ser"] = _gpu_vs_oracle(small, q2, p2, e2, ref2, 2, "SER", "mixed")
@@ -472,7 +474,7 @@ def run_reference(args):
     sub = oracle_sample(w, n_target)
     spec = sub.replicas[0]
     q, p, e = inputs.workload_state(sub, float32=False)
-    S = O.System([O.make_replica(spec.n, spec.box, spec.cv, spec.bricks)],
+    S = O.System([O.make_replica(spec.n, spec.box, spec.cv, spec.bricks, spec.walls, spec.wall_u)],
                  O.make_params(sub.mass, sub.r_cut, sub.a, sub.sigma, sub.seed), q, p, e)
     S.run(args.warmup, sub.dt, args.scheme)
     t = time.perf_counter()

@@ -184,8 +184,20 @@ typedef struct dpde_replica {
     double  box[3];      /* L_x, L_y, L_z > 0                               */
     double  cv;          /* constant heat capacity C_v > 0                  */
     int32_t bricks[3];   /* Hybrid domain grid B_d >= 1 (1,1,1 = one domain) */
-    int32_t reserved;    /* must be 0                                       */
+    int32_t walls;       /* 0: periodic along z; 1: specular walls along z   */
+    double  wall_u;      /* walls = 1: velocity of the upper wall (<= 0)     */
 } dpde_replica;
+
+/* Walls (the confining walls of the shock set-up, Sec. V, read as hard
+ * specular walls). With walls = 1 the replica stays periodic along x and y;
+ * along z it lies between a fixed wall at z = 0 and a wall at
+ * z_w(n) = L_z + wall_u n dt after step n (n the step counter, dt that
+ * step's dt; wall_u < 0 drives it in as a piston). No pair interacts across
+ * the z boundary, and the SSA colours along z are those of a non-periodic
+ * axis. A particle that crosses a wall during the drift is mirrored:
+ * z -> 2 z_w - z and p_z -> 2 m u_w - p_z (u_w = 0 at z = 0). Positions
+ * passed to dpde_set_state must lie in [0, z_w). A step after which the
+ * moving wall would enter the lowest cell layer returns DPDE_ERR_ARG. */
 
 /* Observables of one replica at the current state (Sec. II.B). */
 typedef struct dpde_obs {

@@ -65,6 +65,8 @@ struct dpde_handle {
     int* dom_cell0 = nullptr;    // first cell of each brick, then ncells
     double dom_mean = 0.0;       // most particles per brick of a replica, on average
     int ssa_mode = 0;
+    bool any_walls = false;       // some replica has walls along z
+    WallPos* wallpos = nullptr;   // upper wall of each replica for the step's drift
     int ssa_group = 0;        // bricks per warp; 0 = dom_group_auto
     int dom_group_auto = 1;   // 32 / the largest class of a brick, in 1..SSA_GROUP_MAX
     int hcap = 0;             // halo particles staged per force tile
@@ -132,7 +134,7 @@ Ctx<T> make_ctx(dpde_handle* h) {
     C.fwd_j = h->fwd_j; C.fwd_w = (T*)h->fwd_w; C.fwd_g = (vec_t<T>*)h->fwd_g; C.fwd_n = h->fwd_n;
     C.rep_of_slot = h->rep_of_slot; C.rep_of_cell = h->rep_of_cell;
     C.brick_rep = h->brick_rep; C.tab = h->tab;
-    C.reps = h->d_reps; C.step = h->d_step; C.status = h->d_status;
+    C.reps = h->d_reps; C.step = h->d_step; C.status = h->d_status; C.wall = h->wallpos;
     C.N = h->N; C.ncells = h->ncells;
     C.m = (T)h->prm.mass; C.inv_m = (T)(1.0 / h->prm.mass);
     C.rc = (T)h->prm.r_cut; C.rc2 = (T)(h->prm.r_cut * h->prm.r_cut);
@@ -230,6 +232,7 @@ template <class T>
 void enqueue_step(dpde_handle* h, cudaStream_t st, double dt_d, int scheme) {
     const Ctx<T> C = make_ctx<T>(h);
     const T dt = (T)dt_d, half_dt = (T)(0.5 * dt_d), sqrt_dt = (T)std::sqrt(dt_d);
+    if (h->any_walls) k_wall_pos<T><<<ceil_div(h->R, 64), 64, 0, st>>>(C, h->R, dt_d);
     const int nb = ceil_div(h->N, h->block);
     enqueue_sort<T>(h, C, st, half_dt, dt, 1);
     const int list = scheme == DPDE_SSA ? LIST_FWD : (scheme == DPDE_HYBRID ? LIST_CROSS : LIST_ALL);
@@ -307,6 +310,7 @@ int read_status(dpde_handle* h) {
     CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     if (st & ST_CAPACITY) return fail(h, DPDE_ERR_CAPACITY, "neighbour list capacity exceeded");
+    if (st & ST_WALL) return fail(h, DPDE_ERR_ARG, "the moving wall reached the lowest cell layer");
     if (st & ST_DOMAIN) return fail(h, DPDE_ERR_CUDA, "internal error: an SSA chain left its domain");
     if (st & ST_NONFINITE) return fail(h, DPDE_ERR_NONFINITE, "non-finite value in the state");
     if (st & ST_NEG_EPS) return fail(h, DPDE_ERR_NEG_EPS, "internal energy eps_i <= 0");
@@ -320,7 +324,7 @@ void free_all(dpde_handle* h) {
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
     void* bufs[] = {h->qA, h->pA, h->qB, h->pB, h->F, h->dp, h->upot, h->proj_e0, h->proj_shift, h->proj_partial, h->eA, h->eB, h->nbr_w, h->cA, h->cB, h->nbr_j,
-                    h->nbr_n, h->fwd_j, h->fwd_w, h->fwd_g, h->fwd_n, h->tile_org, h->tile_dim, h->defer, h->col_cells[0], h->col_cells[1], h->dom_cells, h->dom_off, h->dom_cell0, h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
+                    h->nbr_n, h->fwd_j, h->fwd_w, h->fwd_g, h->fwd_n, h->tile_org, h->tile_dim, h->defer, h->col_cells[0], h->col_cells[1], h->dom_cells, h->dom_off, h->dom_cell0, h->wallpos, h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
                     h->rep_of_cell, h->brick_rep, h->tab, h->chunk_rep, h->chunk_begin, h->chunk_end,
                     h->rep_chunk_begin, h->partial, h->obs_out, h->d_reps, h->d_step, h->d_status,
                     h->staging, h->cells_out};
@@ -436,9 +440,13 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     for (int r = 0; r < n_replicas; ++r) {
         const dpde_replica& d = replicas[r];
         RepInfo I{};
-        if (d.n < 0 || d.reserved != 0 || !(d.cv > 0)) {
+        if (d.n < 0 || !(d.cv > 0)) {
             delete h;
             return fail(nullptr, DPDE_ERR_ARG, "replica " + std::to_string(r) + ": bad n/cv");
+        }
+        if ((d.walls != 0 && d.walls != 1) || (d.walls == 1 && !(d.wall_u <= 0.0))) {
+            delete h;
+            return fail(nullptr, DPDE_ERR_ARG, "replica " + std::to_string(r) + ": walls must be 0 or 1, wall_u <= 0");
         }
         for (int a = 0; a < 3; ++a) {
             if (!(d.box[a] > 0) || d.bricks[a] < 1) {
@@ -469,6 +477,9 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         I.tab_off = (int)tabs.size();
         I.cv = d.cv;
         I.cvf = (float)d.cv;
+        I.walls = d.walls;
+        I.wall_u = d.walls ? d.wall_u : 0.0;
+        h->any_walls = h->any_walls || d.walls;
         // brick-major cell tables
         for (int c = 0; c < I.nc[0]; ++c) tabs.push_back((c / I.k[0]) * kc + c % I.k[0]);
         for (int c = 0; c < I.nc[1]; ++c) tabs.push_back((c / I.k[1]) * I.B[0] * kc + (c % I.k[1]) * I.k[0]);
@@ -518,7 +529,7 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
             const int* tz = ty + I.nc[1];
             int col[3][1024];
             for (int a = 0; a < 3; ++a) {
-                const bool periodic = m == 1 || I.B[a] == 1;
+                const bool periodic = (m == 1 || I.B[a] == 1) && !(a == 2 && I.walls);
                 const int k = m == 1 ? I.nc[a] : I.k[a];
                 const int P = a == 2 ? 2 : 3;
                 const int full = P * (k / P);
@@ -630,6 +641,7 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     CKC(cudaMalloc(&h->partial, sizeof(double) * NTERMS * std::max<size_t>(1, chunk_rep.size())));
     CKC(cudaMalloc(&h->obs_out, sizeof(double) * NTERMS * (size_t)h->R));
     CKC(cudaMalloc(&h->d_reps, sizeof(RepInfo) * (size_t)h->R));
+    CKC(cudaMalloc(&h->wallpos, sizeof(WallPos) * (size_t)std::max(1, h->R)));
     CKC(cudaMalloc(&h->d_step, sizeof(long long)));
     CKC(cudaMalloc(&h->d_status, sizeof(unsigned int)));
     CKC(cudaMalloc(&h->staging, sizeof(double) * 7 * n1));

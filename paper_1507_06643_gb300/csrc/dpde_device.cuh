@@ -89,6 +89,15 @@ struct RepInfo {
     int tab_off;     // offset of the replica's cell tables
     double cv;       // C_v
     float cvf;
+    int walls;       // 1: specular walls along z (not periodic along z)
+    double wall_u;   // velocity of the upper wall along z (walls = 1)
+};
+
+// Position of the upper wall of a walled replica for the current step's
+// drift, as a cell index and an offset in it: z_w = c ell_z + o.
+struct WallPos {
+    double o;
+    int c;
     int pad;
 };
 
@@ -239,6 +248,6 @@ template <class T>
 __device__ __forceinline__ T pair_pot_at_zero(const PotT<T>& P) { return P.kind == 1 ? T(0) : P.half_arc; }
 
 // Status bits raised by the kernels (read and cleared by the host).
-enum : unsigned int { ST_NEG_EPS = 1u, ST_NONFINITE = 2u, ST_CAPACITY = 4u, ST_DOMAIN = 8u };
+enum : unsigned int { ST_NEG_EPS = 1u, ST_NONFINITE = 2u, ST_CAPACITY = 4u, ST_DOMAIN = 8u, ST_WALL = 16u };
 
 }  // namespace dpde

@@ -42,6 +42,7 @@ template <class T> struct Ctx {
     const int* tab;
     const RepInfo* reps;
     const long long* step;   // device step counter
+    WallPos* wall;           // upper wall of each replica for this step's drift
     unsigned int* status;
     int N, ncells;
     T m, inv_m, rc, rc2, inv_rc, a, sigma, sig2_4;
@@ -104,6 +105,7 @@ __device__ __forceinline__ void for_each_neighbour(const Ctx<T>& C, const vec_t<
     const bool xcross_m = __ldg(bt + xm) != bx, xcross_p = __ldg(bt + xp) != bx;
     for (int dz = -1; dz <= 1; ++dz) {
         int z = cz + dz;
+        if (R.walls && (z < 0 || z >= nz)) continue;   // nothing beyond a wall
         z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
         const T sz = shift<T>(dz, lz);
         const bool zc = __ldg(bt + nx + ny + z) != bz;
@@ -229,11 +231,82 @@ __device__ __forceinline__ void move_axis(T& o, int& c, T l, int nc) {
     }
 }
 
+// Along a walled z axis: the drifted offset o of cell c, and its momentum
+// p_z, mirrored at the wall z = 0 (z -> -z, p_z -> -p_z) or at the upper wall
+// z_w = W.c l + W.o (z -> 2 z_w - z, p_z -> two_mu - p_z, two_mu = 2 m u),
+// in cell-relative arithmetic.
+template <class T>
+__device__ __forceinline__ void wall_axis(T& o, int& c, T& pz, T l, int nc, const WallPos& W, T two_mu) {
+    int cu = c;
+    T on = o;
+    if (on >= l || on < T(0)) {
+        const T f = tfloor(on / l);
+        on -= f * l;
+        cu += (int)f;
+        if (on >= l) { on -= l; ++cu; }
+    }
+    if (cu < 0) {
+        cu = -cu - 1;
+        on = l - on;
+        if (on >= l) { on -= l; ++cu; }
+        pz = -pz;
+    } else {
+        const T ow = (T)W.o;
+        if (cu > W.c || (cu == W.c && on > ow)) {
+            const T d = (T)(cu - W.c) * l + (on - ow);   // z - z_w > 0
+            T o2 = ow - d;
+            int c2 = W.c;
+            const T f = tfloor(o2 / l);
+            o2 -= f * l;
+            c2 += (int)f;
+            if (o2 >= l) { o2 -= l; ++c2; }
+            cu = c2;
+            on = o2;
+            pz = two_mu - pz;
+        }
+    }
+    // a position exactly on the upper face stays in the top cell
+    if (cu >= nc) { cu = nc - 1; on = l; }
+    if (cu < 0) { cu = 0; on = T(0); }
+    o = on;
+    c = cu;
+}
+
+// Upper-wall position of every replica for the drift of the current step n:
+// z_w = L_z + u (n + 1) dt (L_z for replicas without walls). A wall inside
+// the lowest cell layer raises ST_WALL.
+template <class T>
+__global__ void k_wall_pos(Ctx<T> C, int nrep, double dt) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrep) return;
+    const RepInfo& I = C.reps[r];
+    WallPos w;
+    w.c = I.nc[2];
+    w.o = 0.0;
+    w.pad = 0;
+    if (I.walls && I.wall_u != 0.0) {
+        const double zw = I.L[2] + I.wall_u * (double)(*C.step + 1) * dt;
+        int c = (int)floor(zw * I.s[2]);
+        c = c > I.nc[2] ? I.nc[2] : c;
+        double o = zw - (double)c * I.ell[2];
+        if (o < 0.0) { --c; o += I.ell[2]; }
+        if (c < 1) {
+            flag(C.status, ST_WALL);
+            c = 1;
+            o = 0.0;
+        }
+        w.c = c;
+        w.o = o;
+    }
+    C.wall[r] = w;
+}
+
 template <class T>
 __global__ void k_kick_drift_key(Ctx<T> C, T half_dt, T dt, int kick) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= C.N) return;
-    const RepInfo& R = C.reps[C.rep_of_slot[s]];
+    const int rep = C.rep_of_slot[s];
+    const RepInfo& R = C.reps[rep];
     int cc = C.cA[s];
     int cx = cell_x(cc), cy = cell_y(cc), cz = cell_z(cc);
     if (kick) {
@@ -245,7 +318,10 @@ __global__ void k_kick_drift_key(Ctx<T> C, T half_dt, T dt, int kick) {
         qv.x += c * pv.x; qv.y += c * pv.y; qv.z += c * pv.z;
         move_axis(qv.x, cx, cell_len<T>(R, 0), R.nc[0]);
         move_axis(qv.y, cy, cell_len<T>(R, 1), R.nc[1]);
-        move_axis(qv.z, cz, cell_len<T>(R, 2), R.nc[2]);
+        if (R.walls)
+            wall_axis(qv.z, cz, pv.z, cell_len<T>(R, 2), R.nc[2], C.wall[rep], T(2) * C.m * (T)R.wall_u);
+        else
+            move_axis(qv.z, cz, cell_len<T>(R, 2), R.nc[2]);
         cc = pack_cell(cx, cy, cz);
         C.pA[s] = pv;
         C.qA[s] = qv;
@@ -478,6 +554,7 @@ __device__ void force_one_global(const Ctx<T>& C, int i, T half_dt, int kick) {
     for (int sg = 0; sg < 27; ++sg) {
         const int dxc = sg % 3 - 1, dyc = (sg / 3) % 3 - 1, dzc = sg / 9 - 1;
         int x = cx + dxc, y = cy + dyc, z = cz + dzc;
+        if (R.walls && (z < 0 || z >= nz)) continue;   // nothing beyond a wall
         x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
         y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
         z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
@@ -559,6 +636,12 @@ __device__ __forceinline__ void force_tile_run(const Ctx<T>& C, int tile, const 
     for (int h = threadIdx.x; h < HC; h += blockDim.x) {
         const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
         int x = org.y + hx - 1, y = org.z + hy - 1, z = org.w + hz - 1;
+        if (R.walls && (z < 0 || z >= nz)) {   // beyond a wall: an empty halo cell
+            gstart[h] = 0;
+            hstart[h] = 0;
+            hbrick[h] = -1;
+            continue;
+        }
         x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
         y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
         z = z < 0 ? z + nz : (z >= nz ? z - nz : z);

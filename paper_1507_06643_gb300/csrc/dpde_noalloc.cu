@@ -56,6 +56,7 @@ struct NaGeom {
     int nc[3];
     double rc, rc2, a, mass, cv;
     int n;
+    int walls;   // 1: walls along z (no periodic image along z)
     dpde::PotT<double> pot;
 };
 
@@ -137,6 +138,7 @@ __global__ void k_na_terms(NaGeom G, const double* __restrict__ q, const double*
         for (int dz = -1; dz <= 1; ++dz)
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
+                    if (G.walls && (cz + dz < 0 || cz + dz >= G.nc[2])) continue;
                     const int x = (cx + dx + G.nc[0]) % G.nc[0];
                     const int y = (cy + dy + G.nc[1]) % G.nc[1];
                     const int z = (cz + dz + G.nc[2]) % G.nc[2];
@@ -147,7 +149,7 @@ __global__ void k_na_terms(NaGeom G, const double* __restrict__ q, const double*
                         double d[3], r2 = 0.0;
                         for (int a = 0; a < 3; ++a) {
                             double v = xi[a] - q[3 * j + a];
-                            v -= G.L[a] * rint(v / G.L[a]);
+                            if (!(a == 2 && G.walls)) v -= G.L[a] * rint(v / G.L[a]);
                             d[a] = v;
                             r2 += v * v;
                         }
@@ -201,6 +203,7 @@ int dpde_observables_noalloc(const dpde_params* params, const dpde_replica* repl
     const dpde_params& P = *params;
     const dpde_replica& Rp = *replica;
     if (!(P.mass > 0) || !(P.r_cut > 0) || !(P.a >= 0) || !(Rp.cv > 0) || Rp.n < 0 ||
+        (Rp.walls != 0 && Rp.walls != 1) ||
         (P.potential != DPDE_POT_SOFT && P.potential != DPDE_POT_LJ) ||
         (P.potential == DPDE_POT_LJ && (!(P.lj_eps >= 0) || !(P.lj_r > 0))))
         return na_fail(DPDE_ERR_ARG, "invalid parameters");
@@ -230,6 +233,7 @@ int dpde_observables_noalloc(const dpde_params* params, const dpde_replica* repl
     G.mass = P.mass;
     G.cv = Rp.cv;
     G.n = (int)Rp.n;
+    G.walls = Rp.walls;
     // device address of the scratch array, looked up once per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -45,7 +45,7 @@ class dpde_params(C.Structure):
 
 class dpde_replica(C.Structure):
     _fields_ = [("n", C.c_int64), ("box", C.c_double * 3), ("cv", C.c_double),
-                ("bricks", C.c_int32 * 3), ("reserved", C.c_int32)]
+                ("bricks", C.c_int32 * 3), ("walls", C.c_int32), ("wall_u", C.c_double)]
 
 
 class dpde_obs(C.Structure):
@@ -273,7 +273,8 @@ def make_params(mass=1.0, r_cut=1.0, a=25.0, sigma=3.0, seed=0, precision="mixed
                        lj_eps, lj_r)
 
 
-def make_replica(n, box, cv, bricks=(1, 1, 1)) -> dpde_replica:
+def make_replica(n, box, cv, bricks=(1, 1, 1), walls=0, wall_u=0.0) -> dpde_replica:
+    """walls = 1: specular walls along z at 0 and L_z + wall_u n dt (dpde.h)."""
     if np.isscalar(box):
         box = (box, box, box)
     r = dpde_replica()
@@ -281,7 +282,8 @@ def make_replica(n, box, cv, bricks=(1, 1, 1)) -> dpde_replica:
     r.box[:] = [float(x) for x in box]
     r.cv = float(cv)
     r.bricks[:] = [int(b) for b in bricks]
-    r.reserved = 0
+    r.walls = int(walls)
+    r.wall_u = float(wall_u)
     return r
 
 

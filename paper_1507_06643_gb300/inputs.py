@@ -28,6 +28,9 @@ class ReplicaSpec:
     kT: float = 1.0
     bricks: tuple = (1, 1, 1)
     vz_split: float = 0.0     # +v for z < Lz/2, -v above (shock set-up)
+    vz_shift: float = 0.0     # v added to every particle along z (piston set-up)
+    walls: int = 0            # 1: specular walls along z (see the library header)
+    wall_u: float = 0.0       # velocity of the upper wall (walls = 1)
 
 
 @dataclasses.dataclass
@@ -66,6 +69,8 @@ def replica_state(spec: ReplicaSpec, mass: float, rng: np.random.Generator,
         p -= p.mean(axis=0, keepdims=True)
     if spec.vz_split and n > 0:
         p[:, 2] += np.where(q[:, 2] < 0.5 * box[2], spec.vz_split, -spec.vz_split) * mass
+    if spec.vz_shift and n > 0:
+        p[:, 2] += spec.vz_shift * mass
     eps = spec.cv * spec.kT * (1.0 + eps_spread * rng.uniform(-1.0, 1.0, n))
     if float32:
         q = q.astype(np.float32).astype(np.float64)
@@ -128,6 +133,19 @@ def shock_40x40x800(precision: str = "mixed") -> Workload:
                     dt=0.005, steps=20000, seed=1004, precision=precision)
 
 
+def shock_walls_40x40x800(precision: str = "mixed") -> Workload:
+    """The shock set-up of Sec. V in its hard-wall reading: box 40 x 40 x 800
+    at density 3 (3.84M particles), periodic along x and y, walls along z --
+    fixed at z = 0, the upper one moving at u_p = -2 -- and every particle
+    given v_z = u_p on a kT=1 Maxwellian, so that a shock runs up from the
+    fixed wall; C_v=100, dt=0.005; Hybrid domains 8x8x160."""
+    n = 3 * 40 * 40 * 800
+    return Workload("shock_walls_40x40x800",
+                    [ReplicaSpec(n, (40.0, 40.0, 800.0), 100.0, 1.0, (8, 8, 160), vz_shift=-2.0, walls=1,
+                                 wall_u=-2.0)],
+                    dt=0.005, steps=20000, seed=1007, precision=precision)
+
+
 def batched_256(precision: str = "mixed", n_replicas: int = 256, seed: int = 1005,
                 n_min: int = 2000, n_max: int = 64000) -> Workload:
     """256 independent systems, n_r log-uniform in [2000, 64000] at density 3,
@@ -171,5 +189,6 @@ WORKLOADS = {
     "large_n4m": large_n4m,
     "medium_n1m": medium_n1m,
     "shock_40x40x800": shock_40x40x800,
+    "shock_walls_40x40x800": shock_walls_40x40x800,
     "batched_256": batched_256,
 }

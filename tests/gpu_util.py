@@ -65,16 +65,17 @@ def oracle_cells(q, specs, offsets, r_cut=1.0):
 
 
 def run_both(specs, precision, scheme, nsteps, dt=0.01, seed=1, a=25.0, sigma=3.0, prm_seed=42,
-             use_graph=True, state=None, r_cut=1.0, pot=None):
+             use_graph=True, state=None, r_cut=1.0, pot=None, walls=(0, 0.0)):
     """Runs both sides step by step. Returns (errs, flips, gpu_state, ref) where
     flips is the set of particles whose cell differed between the two sides at
-    some step (the per-step decision positions are the end-of-step positions)."""
+    some step (the per-step decision positions are the end-of-step positions).
+    walls = (walls, wall_u) of every replica."""
     q, p, e = state if state is not None else make_state(specs, seed, precision == "mixed")
-    reps = [dpde.make_replica(n, box, cv, br) for n, box, cv, _, br in specs]
+    reps = [dpde.make_replica(n, box, cv, br, *walls) for n, box, cv, _, br in specs]
     pot = pot or {}
     S = dpde.System(dpde.make_params(1.0, r_cut, a, sigma, prm_seed, precision, **pot), reps)
     S.set_state(q, p, e)
-    oreps = [O.make_replica(n, box, cv, br) for n, box, cv, _, br in specs]
+    oreps = [O.make_replica(n, box, cv, br, *walls) for n, box, cv, _, br in specs]
     ref = O.System(oreps, O.make_params(1.0, r_cut, a, sigma, prm_seed, **pot), q, p, e)
     flips = set()
     for _ in range(nsteps):

@@ -107,6 +107,60 @@ def test_parity_sizes(n, box, bricks, scheme, precision):
         break
 
 
+# ---- walls along z (the shock set-up's confining walls, Sec. V) ---------------------------
+
+@pytest.mark.parametrize("wall_u", [0.0, -1.5])
+@pytest.mark.parametrize("scheme,bricks", [("SER", (1, 1, 1)), ("HYBRID", (2, 2, 3)), ("SSA", (1, 1, 1)),
+                                           ("SEM", (1, 1, 1)), ("HYBRID", (1, 1, 1))])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_parity_walls(precision, scheme, bricks, wall_u):
+    # a flux into both walls, a piston moving in, 12 steps
+    specs = [(1600, (7.0, 7.0, 10.5), 50.0, 1.0, bricks)]
+    for errs, gpu, ref in assert_parity(specs, precision, scheme, 12, TOL[precision],
+                                        seeds=range(700, 708), walls=(1, wall_u)):
+        qg = gpu[0]
+        zw = 10.5 + wall_u * 12 * 0.01
+        assert np.all(qg[:, 2] >= 0.0) and np.all(qg[:, 2] <= zw + 1e-6)
+        break
+
+
+def test_walled_replicas_beside_periodic_ones():
+    # one launch over a walled and a periodic replica: each matches its own oracle run
+    from paper_1507_06643_gb300 import dpde
+    from oracle import oracle as O
+    specs = [(900, (6.5, 6.5, 7.2), 50.0, 1.0, (1, 1, 2)), (700, (6.0, 6.0, 6.4), 50.0, 1.0, (1, 1, 1))]
+    q, p, e = make_state(specs, 55, True)
+    reps = [dpde.make_replica(900, (6.5, 6.5, 7.2), 50.0, (1, 1, 2), 1, -0.5),
+            dpde.make_replica(700, (6.0, 6.0, 6.4), 50.0, (1, 1, 1))]
+    S = dpde.System(dpde.make_params(precision="fp64", seed=9), reps)
+    S.set_state(q, p, e)
+    S.step(8, 0.01, "HYBRID")
+    qg, pg, eg = S.get_state()
+    S.close()
+    oreps = [O.make_replica(900, (6.5, 6.5, 7.2), 50.0, (1, 1, 2), 1, -0.5),
+             O.make_replica(700, (6.0, 6.0, 6.4), 50.0, (1, 1, 1))]
+    ref = O.System(oreps, O.make_params(seed=9), q, p, e)
+    ref.run(8, 0.01, "HYBRID")
+    assert rel_err(pg, ref.p) < 1e-11 and rel_err(eg, ref.eps) < 1e-11
+
+
+def test_piston_overrun_and_bad_walls_reported():
+    from paper_1507_06643_gb300 import dpde
+    # a sparse fluid (no neighbour-list overflow while it is squeezed)
+    rep = dpde.make_replica(60, (4.0, 4.0, 4.0), 50.0, walls=1, wall_u=-20.0)
+    q, p, e = make_state([(60, (4.0, 4.0, 4.0), 50.0, 1.0, (1, 1, 1))], 3, False)
+    S = dpde.System(dpde.make_params(precision="fp64"), [rep])
+    S.set_state(q, p, e)
+    S.step(10, 0.01, "SER")              # z_w = 4 - 0.2 (n + 1) > 1: still fine
+    assert S.sync() == dpde.DPDE_OK
+    S.step(10, 0.01, "SER")              # the wall passes z = ell_z = 1 at n = 15
+    assert S.sync() == dpde.DPDE_ERR_ARG
+    S.close()
+    for w, u in ((2, 0.0), (1, 0.5)):
+        with pytest.raises(dpde.DPDEError):
+            dpde.System(dpde.make_params(), [dpde.make_replica(300, (4.0, 4.0, 4.0), 50.0, walls=w, wall_u=u)])
+
+
 def slab_state(seed, L=12.0, rho=3.0, rho_slab=9.0, slab=4.0, float32=False):
     """Uniform fluid at rho with a slab z < `slab` at rho_slab: cells there
     hold ~3x the mean, so SSA chains overflow the per-cell row table and the
