@@ -54,3 +54,30 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(torch_cuda):
                                       None, None, None)
     assert ei.value.code == dpde.DPDE_ERR_ARG
     assert "scratch limit" in str(ei.value)
+
+
+def test_noalloc_observables_with_walls(torch_cuda):
+    """A replica with walls along z: no pair across the z boundary, as in the
+    handle and in the oracle (the potential energy differs from the periodic
+    box's)."""
+    torch = torch_cuda
+    from oracle import oracle as O
+    from paper_1507_06643_gb300 import dpde
+    n, box = 6000, (11.0, 11.0, 16.6)
+    q, p, e = make_state([(n, box, 100.0, 1.0, (1, 1, 1))], 21, False)
+    prm = dpde.make_params(precision="fp64")
+    rep = dpde.make_replica(n, box, 100.0, walls=1)
+    S = dpde.System(prm, [rep])
+    S.set_state(q, p, e)
+    ref = S.observables(check=True)[0]
+    S.close()
+    ora = O.System([O.make_replica(n, box, 100.0, walls=1)], O.make_params(), q, p, e).observables()
+    periodic = O.System([O.make_replica(n, box, 100.0)], O.make_params(), q, p, e).observables()
+    qd, pd, ed = (torch.from_numpy(x).cuda() for x in (q, p, e))
+    torch.cuda.synchronize()
+    rc, got = dpde.dpde_observables_noalloc(prm, rep, qd, pd, ed)
+    assert rc == dpde.DPDE_OK
+    for k in ("E", "U", "Tpot_num", "Tpot_den"):
+        assert abs(got[k] - ref[k]) <= 1e-10 * abs(ref[k]), (k, got[k], ref[k])
+        assert abs(got[k] - ora[k]) <= 1e-10 * abs(ora[k]), (k, got[k], ora[k])
+    assert abs(got["U"] - periodic["U"]) > 1e-6 * abs(periodic["U"])
