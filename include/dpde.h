@@ -367,7 +367,8 @@ typedef struct dpde_tuning {
     int32_t tile_edge;   /* force tile edge in cells, 2..8 (default 6)                */
     int32_t block;       /* threads per block of the per-particle kernels: a multiple  */
                          /* of 32 in 64..1024 (default 256)                           */
-    int32_t ssa_block;   /* threads per block of the SSA launches: 32, 64, 96 or 128   */
+    int32_t ssa_block;   /* threads per block of the per-class SSA launches: 32, 64,   */
+                         /* 96 or 128 (the per-domain form runs one warp per block)    */
                          /* (default 64)                                               */
     int32_t ssa_mode;    /* form of the SSA launches; both give the same results bit  */
                          /* for bit. 0 (default): one launch per colour class, a      */

@@ -206,7 +206,9 @@ void enqueue_ssa(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_
     if (!whole && h->ssa_mode == 1 && h->nbricks > 0) {
         const int group = h->ssa_group > 0 ? h->ssa_group : h->dom_group_auto;
         const int warps = ceil_div(h->nbricks, group);
-        const int wpb = h->ssa_block / 32;
+        // one warp per block: the warps share nothing, and single-warp blocks
+        // pack the staged shared memory without splitting a wave
+        const int wpb = 1;
         // staged slots per warp: the group's mean particle count + 25 % + 64,
         // as far as the shared memory of a block allows
         const size_t per_slot = sizeof(vec_t<T>) + sizeof(eps_t<T>);
@@ -214,7 +216,7 @@ void enqueue_ssa(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_
         long long scap = ((long long)std::ceil(1.25 * group * h->dom_mean) + 64 + 31) / 32 * 32;
         const long long fit = ((long long)(SSA_DOMAIN_SMEM / wpb) - (long long)fixed) / (long long)per_slot;
         scap = std::max(0ll, std::min(scap, fit / 32 * 32));
-        k_ssa_domains<T><<<ceil_div(warps, wpb), h->ssa_block, wpb * ssa_domain_warp_bytes<T>(group, (int)scap), st>>>(
+        k_ssa_domains<T><<<ceil_div(warps, wpb), 32 * wpb, wpb * ssa_domain_warp_bytes<T>(group, (int)scap), st>>>(
             C, h->dom_cells, h->dom_off, h->dom_cell0, h->nbricks, group, (int)scap, dt, sqrt_dt);
         phase(h, st, DPDE_PHASE_SSA, 1);
         return;
