@@ -42,6 +42,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(values, world: int, device="cuda"):
+    """Elementwise maximum of per-rank scalars over all ranks of the process
+    group (the slowest rank sets a time); the values themselves at world = 1."""
+    if world == 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(n_per_rank: int, world: int, steps: int, seconds: float) -> float:
+    """Particle-steps per second of the whole job: every rank advances its
+    own n_per_rank particles (weak scaling) in the slowest rank's time."""
+    return n_per_rank * world * steps / seconds
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -205,14 +223,12 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
     status = S.sync()
-    ms_t = torch.tensor([ms], device="cuda")
+    ms = max_over_ranks([ms], world)[0]
     if world > 1:
-        tdist.all_reduce(ms_t, op=tdist.ReduceOp.MAX)
         tdist.barrier()
-    ms = float(ms_t.item())
     obs1 = S.observables()
     n_tot = w.n_total
-    value = n_tot * world * args.steps / (ms / 1e3)
+    value = whole_job_rate(n_tot, world, args.steps, ms / 1e3)
 
     # per-phase kernel times (CUDA events on the launching stream, eager launches)
     phases = S.step_profiled(args.profile_steps, dt, args.scheme)
@@ -241,10 +257,10 @@ def run_ours(args):
         # (state still advanced); anything else stops the run
         if rc not in (dpde.DPDE_OK, dpde.DPDE_ERR_NEG_EPS):
             raise RuntimeError(f"end-to-end step failed: {rc} {dpde.lib().dpde_last_error(S2.h).decode()}")
-    e2e_s = time.perf_counter() - tt
+    e2e_s = max_over_ranks([time.perf_counter() - tt], world)[0]
     e2e_status = rc
     S2.close()
-    e2e = {"value": n_tot * world * e2e_steps / e2e_s, "unit": UNIT,
+    e2e = {"value": whole_job_rate(n_tot, world, e2e_steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(q.nbytes + p.nbytes + e.nbytes),
            "d2h_bytes_per_step": int(q.nbytes + p.nbytes + e.nbytes), "status": e2e_status}
 
