@@ -405,9 +405,11 @@ int dpde_autotune(dpde_handle* h, int32_t scheme, double dt, int32_t steps, dpde
 
 /* Number of kernel launches in one step of `scheme` (the kernel nodes of
  * the step's CUDA graph, captured here without being run; *launches, host
- * pointer). The count depends on the handle's geometry: the SSA part has one
- * launch drawing the Gaussians, then one per non-empty cell colour class. No device work; the handle's state
- * and step counter are unchanged. DPDE_ERR_ARG for a bad scheme. */
+ * pointer). The count depends on the handle's geometry and tuning: the SSA
+ * part has one launch drawing the Gaussians, then one per non-empty cell
+ * colour class (ssa_mode 0, or DPDE_SSA) or one for all domains (Hybrid in
+ * ssa_mode 1). No device work; the handle's state and step counter are
+ * unchanged. DPDE_ERR_ARG for a bad scheme. */
 int dpde_step_launches(dpde_handle* h, int32_t scheme, int64_t* launches);
 
 /* Cell coordinates (cx, cy, cz) of every particle in id order (3N int32,
