@@ -144,6 +144,25 @@ def test_walled_replicas_beside_periodic_ones():
     assert rel_err(pg, ref.p) < 1e-11 and rel_err(eg, ref.eps) < 1e-11
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_walled_ssa_forms_agree_bit_for_bit(precision):
+    # non-periodic z colours in both SSA forms; bricks one and several along z
+    from paper_1507_06643_gb300 import dpde
+    specs = [(1500, (7.0, 7.0, 10.3), 50.0, 1.0, (1, 1, 3)), (800, (5.5, 5.5, 9.1), 50.0, 1.0, (1, 1, 1))]
+    q, p, e = make_state(specs, 64, precision == "mixed")
+    outs = []
+    for mode in (0, 1):
+        S = dpde.System(dpde.make_params(precision=precision),
+                        [dpde.make_replica(n, box, cv, br, 1, -0.7) for n, box, cv, _, br in specs])
+        S.set_tuning(ssa_mode=mode)
+        S.set_state(q, p, e)
+        S.step(6, 0.01, "HYBRID")
+        outs.append(S.get_state())
+        S.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
 def test_piston_overrun_and_bad_walls_reported():
     from paper_1507_06643_gb300 import dpde
     # a sparse fluid (no neighbour-list overflow while it is squeezed)
