@@ -163,6 +163,34 @@ def test_walled_ssa_forms_agree_bit_for_bit(precision):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_state_through_device_pointers_equals_host_path(precision):
+    # set_state / get_state with torch CUDA tensors (on_device = 1) and with
+    # host arrays give the same state bit for bit, after steps too
+    torch = pytest.importorskip("torch")
+    from paper_1507_06643_gb300 import dpde
+    specs = [(3000, (cube(3000),) * 3, 50.0, 1.0, (2, 2, 2)), (1200, (cube(1200),) * 3, 80.0, 1.0, (1, 1, 1))]
+    q, p, e = make_state(specs, 71, precision == "mixed")
+    reps = [dpde.make_replica(n, box, cv, br) for n, box, cv, _, br in specs]
+    A = dpde.System(dpde.make_params(precision=precision), reps)
+    A.set_state(q, p, e)
+    B = dpde.System(dpde.make_params(precision=precision), reps)
+    qd, pd, ed = (torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (q, p, e))
+    torch.cuda.synchronize()
+    B.set_state(qd, pd, ed, on_device=True)
+    for S in (A, B):
+        S.step(3, 0.01, "HYBRID")
+    qa, pa, ea = A.get_state()
+    qo, po, eo = (torch.empty_like(x) for x in (qd, pd, ed))
+    torch.cuda.synchronize()
+    assert dpde.dpde_get_state(B.h, qo, po, eo, True) == dpde.DPDE_OK
+    torch.cuda.synchronize()
+    for a, b in ((qa, qo), (pa, po), (ea, eo)):
+        assert np.array_equal(a, b.cpu().numpy())
+    A.close()
+    B.close()
+
+
 def test_piston_overrun_and_bad_walls_reported():
     from paper_1507_06643_gb300 import dpde
     # a sparse fluid (no neighbour-list overflow while it is squeezed)
