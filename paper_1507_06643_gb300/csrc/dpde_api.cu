@@ -30,6 +30,8 @@ struct GraphKey {
 
 }  // namespace
 
+constexpr int STATE_CHUNKS = 4;   // chunks of a host <-> device state transfer
+
 struct dpde_handle {
     dpde_params prm{};
     int R = 0;
@@ -44,6 +46,10 @@ struct dpde_handle {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t cap_stream = nullptr;
+    // host <-> device state transfers: copies on their own stream, in chunks,
+    // overlapping the conversion kernels of the neighbouring chunks
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t xfer_ev[STATE_CHUNKS + 1] = {};
     // device buffers
     void *qA = nullptr, *pA = nullptr, *qB = nullptr, *pB = nullptr, *F = nullptr, *dp = nullptr;
     void* upot = nullptr;            // per-particle potential energy share (T)
@@ -279,22 +285,76 @@ void enqueue_step_any(dpde_handle* h, cudaStream_t st, double dt, int scheme) {
     else enqueue_step<double>(h, st, dt, scheme);
 }
 
+// The state in: from device arrays, or from host arrays copied into the
+// staging buffer chunk by chunk on the copy stream, each chunk converted as
+// soon as it has arrived.
 template <class T>
-void enqueue_set_state(dpde_handle* h, cudaStream_t st, const double* q, const double* p, const double* e) {
+void enqueue_set_state(dpde_handle* h, cudaStream_t st, const double* q, const double* p, const double* e,
+                       bool host) {
     const Ctx<T> C = make_ctx<T>(h);
+    const long long N = h->N;
     const int nb = ceil_div(h->N, h->block);
-    k_load_state<T><<<nb, h->block, 0, st>>>(C, q, p, e);
+    const int K = host && N >= (1 << 16) ? STATE_CHUNKS : 1;
+    const double *dq = q, *dp = p, *de = e;
+    if (host) {
+        dq = h->staging; dp = h->staging + 3 * N; de = h->staging + 6 * N;
+        cudaEventRecord(h->xfer_ev[STATE_CHUNKS], st);   // the staging buffer is free
+        cudaStreamWaitEvent(h->copy_stream, h->xfer_ev[STATE_CHUNKS], 0);
+    }
+    for (int c = 0; c < K; ++c) {
+        const long long s0 = N * c / K, s1 = N * (c + 1) / K;
+        if (s1 == s0) continue;
+        if (host) {
+            const size_t n = (size_t)(s1 - s0);
+            cudaMemcpyAsync(h->staging + 3 * s0, q + 3 * s0, sizeof(double) * 3 * n, cudaMemcpyHostToDevice,
+                            h->copy_stream);
+            cudaMemcpyAsync(h->staging + 3 * N + 3 * s0, p + 3 * s0, sizeof(double) * 3 * n,
+                            cudaMemcpyHostToDevice, h->copy_stream);
+            cudaMemcpyAsync(h->staging + 6 * N + s0, e + s0, sizeof(double) * n, cudaMemcpyHostToDevice,
+                            h->copy_stream);
+            cudaEventRecord(h->xfer_ev[c], h->copy_stream);
+            cudaStreamWaitEvent(st, h->xfer_ev[c], 0);
+        }
+        k_load_state<T><<<ceil_div((int)(s1 - s0), h->block), h->block, 0, st>>>(C, dq, dp, de, (int)s0, (int)s1);
+    }
     enqueue_sort<T>(h, C, st, T(0), T(0), 0);
     enqueue_force<T>(h, C, st, T(0), 0, LIST_NONE);
     k_copy_back<T><<<nb, h->block, 0, st>>>(C);
 }
 
+// The state out: into device arrays, or into host arrays through the
+// staging buffer, each chunk of ids copied while the next is gathered; st
+// waits for the copies at the end.
 template <class T>
-void enqueue_get_state(dpde_handle* h, cudaStream_t st, double* q, double* p, double* e) {
+void enqueue_get_state(dpde_handle* h, cudaStream_t st, double* q, double* p, double* e, bool host) {
     const Ctx<T> C = make_ctx<T>(h);
+    const long long N = h->N;
     // the sort's scratch (tmp, N ints) holds the id -> slot map between steps
     k_slot_of_id<T><<<ceil_div(h->N, h->block), h->block, 0, st>>>(C, h->tmp);
-    k_get_state<T><<<ceil_div(h->N, h->block), h->block, 0, st>>>(C, h->tmp, q, p, e);
+    const int K = host && N >= (1 << 16) ? STATE_CHUNKS : 1;
+    double* dq = host ? (q ? h->staging : nullptr) : q;
+    double* dp = host ? (p ? h->staging + 3 * N : nullptr) : p;
+    double* de = host ? (e ? h->staging + 6 * N : nullptr) : e;
+    for (int c = 0; c < K; ++c) {
+        const long long g0 = N * c / K, g1 = N * (c + 1) / K;
+        if (g1 == g0) continue;
+        k_get_state<T><<<ceil_div((int)(g1 - g0), h->block), h->block, 0, st>>>(C, h->tmp, dq, dp, de, (int)g0,
+                                                                              (int)g1);
+        if (host) {
+            const size_t n = (size_t)(g1 - g0);
+            cudaEventRecord(h->xfer_ev[c], st);
+            cudaStreamWaitEvent(h->copy_stream, h->xfer_ev[c], 0);
+            if (q) cudaMemcpyAsync(q + 3 * g0, dq + 3 * g0, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost,
+                                   h->copy_stream);
+            if (p) cudaMemcpyAsync(p + 3 * g0, dp + 3 * g0, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost,
+                                   h->copy_stream);
+            if (e) cudaMemcpyAsync(e + g0, de + g0, sizeof(double) * n, cudaMemcpyDeviceToHost, h->copy_stream);
+        }
+    }
+    if (host) {
+        cudaEventRecord(h->xfer_ev[STATE_CHUNKS], h->copy_stream);
+        cudaStreamWaitEvent(st, h->xfer_ev[STATE_CHUNKS], 0);
+    }
 }
 
 template <class T>
@@ -333,6 +393,9 @@ void free_all(dpde_handle* h) {
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    for (auto& ev : h->xfer_ev)
+        if (ev) cudaEventDestroy(ev);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -603,6 +666,8 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         h->own_stream = true;
     }
     CKC(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    CKC(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    for (auto& ev : h->xfer_ev) CKC(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     const size_t n1 = (size_t)std::max(1, h->N), c1 = (size_t)std::max(1, h->ncells);
     const size_t tsz = h->mixed ? sizeof(float) : sizeof(double);
     CKC(cudaMalloc(&h->qA, vsz * n1));
@@ -714,17 +779,10 @@ int dpde_set_state(dpde_handle* h, const double* q, const double* p, const doubl
     if (!h) return DPDE_ERR_ARG;
     if (h->N > 0 && (!q || !p || !eps)) return fail(h, DPDE_ERR_ARG, "q, p and eps are required");
     const size_t N = (size_t)h->N;
-    const double *dq = q, *dpp = p, *de = eps;
     CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream));
-    if (!on_device && N > 0) {
-        CK(h, cudaMemcpyAsync(h->staging, q, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream));
-        CK(h, cudaMemcpyAsync(h->staging + 3 * N, p, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, h->stream));
-        CK(h, cudaMemcpyAsync(h->staging + 6 * N, eps, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
-        dq = h->staging; dpp = h->staging + 3 * N; de = h->staging + 6 * N;
-    }
     if (N > 0) {
-        if (h->mixed) enqueue_set_state<float>(h, h->stream, dq, dpp, de);
-        else enqueue_set_state<double>(h, h->stream, dq, dpp, de);
+        if (h->mixed) enqueue_set_state<float>(h, h->stream, q, p, eps, !on_device);
+        else enqueue_set_state<double>(h, h->stream, q, p, eps, !on_device);
     }
     long long s = step;
     CK(h, cudaMemcpyAsync(h->d_step, &s, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
@@ -738,17 +796,9 @@ int dpde_get_state(dpde_handle* h, double* q, double* p, double* eps, int32_t on
     if (!h) return DPDE_ERR_ARG;
     const size_t N = (size_t)h->N;
     if (N > 0) {
-        double* dq = on_device ? q : (q ? h->staging : nullptr);
-        double* dpp = on_device ? p : (p ? h->staging + 3 * N : nullptr);
-        double* de = on_device ? eps : (eps ? h->staging + 6 * N : nullptr);
-        if (h->mixed) enqueue_get_state<float>(h, h->stream, dq, dpp, de);
-        else enqueue_get_state<double>(h, h->stream, dq, dpp, de);
+        if (h->mixed) enqueue_get_state<float>(h, h->stream, q, p, eps, !on_device);
+        else enqueue_get_state<double>(h, h->stream, q, p, eps, !on_device);
         CK(h, cudaGetLastError());
-        if (!on_device) {
-            if (q) CK(h, cudaMemcpyAsync(q, h->staging, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, h->stream));
-            if (p) CK(h, cudaMemcpyAsync(p, h->staging + 3 * N, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, h->stream));
-            if (eps) CK(h, cudaMemcpyAsync(eps, h->staging + 6 * N, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream));
-        }
     }
     CK(h, cudaStreamSynchronize(h->stream));
     return read_status(h);

@@ -149,9 +149,9 @@ __device__ __forceinline__ void for_each_neighbour(const Ctx<T>& C, const vec_t<
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void k_load_state(Ctx<T> C, const double* __restrict__ q, const double* __restrict__ p,
-                             const double* __restrict__ e) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= C.N) return;
+                             const double* __restrict__ e, int s0, int s1) {
+    const int s = s0 + blockIdx.x * blockDim.x + threadIdx.x;   // slots s0 .. s1 - 1
+    if (s >= s1) return;
     const RepInfo& R = C.reps[C.rep_of_slot[s]];
     vec_t<T> qv, pv;
     int c[3];
@@ -191,9 +191,9 @@ __global__ void k_slot_of_id(Ctx<T> C, int* __restrict__ slot_of) {
 // FP64 outputs are written contiguously
 template <class T>
 __global__ void k_get_state(Ctx<T> C, const int* __restrict__ slot_of, double* __restrict__ q,
-                            double* __restrict__ p, double* __restrict__ e) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= C.N) return;
+                            double* __restrict__ p, double* __restrict__ e, int g0, int g1) {
+    const int g = g0 + blockIdx.x * blockDim.x + threadIdx.x;   // ids g0 .. g1 - 1
+    if (g >= g1) return;
     const int s = slot_of[g];
     const RepInfo& R = C.reps[C.rep_of_slot[s]];
     if (q) {
