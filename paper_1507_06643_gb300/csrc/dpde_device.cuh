@@ -62,8 +62,6 @@ __device__ __forceinline__ ff ff_add(ff a, float b) {
 }
 __device__ __forceinline__ double eps_value(double e) { return e; }
 __device__ __forceinline__ double eps_value(ff e) { return (double)e.hi + (double)e.lo; }
-__device__ __forceinline__ float eps_approx(ff e) { return e.hi + e.lo; }
-__device__ __forceinline__ double eps_approx(double e) { return e; }
 __device__ __forceinline__ void eps_from(double v, double& e) { e = v; }
 __device__ __forceinline__ void eps_from(double v, ff& e) {
     e.hi = (float)v;

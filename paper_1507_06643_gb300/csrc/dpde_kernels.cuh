@@ -53,9 +53,6 @@ template <class T> struct Ctx {
 // ---------------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------------
-template <class T> __device__ __forceinline__ T tsqrt(T x);
-template <> __device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
-template <> __device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
 template <class T> __device__ __forceinline__ T texpm1(T x);
 template <> __device__ __forceinline__ float texpm1(float x) { return expm1f(x); }
 template <> __device__ __forceinline__ double texpm1(double x) { return expm1(x); }
