@@ -99,11 +99,17 @@ def test_replicas_are_independent(ora):
     assert not np.array_equal(both.p[300:], alone2.p)
 
 
-@pytest.mark.parametrize("scheme,dt,tol", [("SSA", 0.01, 0.04), ("HYBRID", 0.01, 0.04),
-                                           ("SER", 0.005, 0.05)])
-def test_equilibrium_kinetic_equals_internal_temperature(ora, scheme, dt, tol):
+@pytest.mark.parametrize("scheme,dt,tol,kT", [("SSA", 0.01, 0.04, 1.0), ("HYBRID", 0.01, 0.04, 1.0),
+                                              ("SSA", 0.01, 0.04, 2.0), ("HYBRID", 0.01, 0.04, 2.0),
+                                              ("SER", 0.005, 0.05, 2.0)])
+def test_equilibrium_kinetic_equals_internal_temperature(ora, scheme, dt, tol, kT):
+    """At kT = 1 every beta_i = C_v / eps_i is close to T_i = eps_i / C_v, so
+    only the run at kT = 2 (beta ~ 1/2, T ~ 2) tells the fluctuation/
+    dissipation relation Eq. (DPDE_fd), gamma ~ 1/T_i + 1/T_j, from a wrong
+    one: with gamma ~ T_i + T_j the kinetic temperature would settle near
+    1/T_int instead of T_int."""
     n, box = 300, (4.64,) * 3
-    q, p, eps = state(n, box, seed=36, cv=10.0)
+    q, p, eps = state(n, box, seed=36, cv=10.0, kT=kT)
     rep = ora.make_replica(n, box, 10.0, (2, 1, 1))
     S = ora.System([rep], ora.make_params(sigma=3.0, seed=3), q, p, eps)
     S.run(int(5.0 / dt), dt, scheme)              # relax
@@ -115,6 +121,37 @@ def test_equilibrium_kinetic_equals_internal_temperature(ora, scheme, dt, tol):
         ti.append(o["Tint"])
     tk, ti = np.mean(tk), np.mean(ti)
     assert abs(tk / ti - 1) < tol, (tk, ti)
+    assert kT < tk < 1.5 * kT, tk                  # heated a little by the relaxing overlaps
+
+
+def test_equilibrium_internal_energies_are_gamma_distributed(ora):
+    """Canonical measure of the internal energies (Sec. IV.B; the invariant
+    measure Eq. (DPDE_invariant_measure_general) with s'(eps) = 1/T(eps) =
+    C_v / eps): eps_i has density ~ eps^C_v exp(-eps / k_B T), the Gamma law of
+    shape C_v + 1 and scale k_B T. Its scale must equal the kinetic
+    temperature, and its shape is checked by the relative variance 1/(C_v + 1)
+    and a Kolmogorov-Smirnov distance. Run at kT = 2, where beta_i and T_i
+    differ."""
+    stats = pytest.importorskip("scipy.stats")
+    n, box, cv, dt = 300, (4.64,) * 3, 10.0, 0.01
+    q, p, eps = state(n, box, seed=37, cv=cv, kT=2.0)
+    rep = ora.make_replica(n, box, cv, (1, 1, 1))
+    S = ora.System([rep], ora.make_params(sigma=3.0, seed=4), q, p, eps)
+    S.run(500, dt, "SSA")
+    samples, tk = [], []
+    for _ in range(150):
+        S.run(40, dt, "SSA")
+        samples.append(S.eps.copy())
+        tk.append(S.observables()["Tkin"])
+    e = np.concatenate(samples)
+    theta = e.mean() / (cv + 1.0)
+    assert abs(theta / np.mean(tk) - 1) < 0.03, (theta, np.mean(tk))
+    rel_var = e.var() / e.mean() ** 2
+    assert abs(rel_var * (cv + 1.0) - 1) < 0.06, rel_var      # shape C_v would give 1.1
+    D = stats.kstest(e, stats.gamma(cv + 1.0, scale=theta).cdf).statistic
+    D_wrong = stats.kstest(e, stats.gamma(cv, scale=e.mean() / cv).cdf).statistic
+    assert D < 0.03, D
+    assert D_wrong > 2 * D, (D, D_wrong)
 
 
 # ---- projection on the internal energies (Sec. IV.C) ---------------------------

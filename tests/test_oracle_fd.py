@@ -64,6 +64,67 @@ def test_ssa_hand_case(ora):
     assert np.allclose(e1 - eps, [-dK / 2, -dK / 2], atol=3e-14, rtol=0)
 
 
+# Unequal internal temperatures pin gamma_ij = sigma^2/4 (1/T_i + 1/T_j) of
+# Eq. (DPDE_fd) with T_i = eps_i / C_v (Eq. DPDE_internalEOS at constant C_v).
+# The cases are chosen so that 1/T_i + 1/T_j differs from T_i + T_j, from
+# 2 / mean(T) and from the equal-temperature value: a formula using T in place
+# of beta, or dropping one particle's term, fails them.
+#   cv = 100, eps = (200, 100): beta = (1/2, 1),  gamma = 9/4 * 3/2 = 27/8
+#   cv =  50, eps = (25, 200):  beta = (2, 1/4),  gamma = 9/4 * 9/4 = 81/16
+UNEQUAL_T = [
+    # cv, eps_i, eps_j, gamma
+    (100.0, 200.0, 100.0, 27.0 / 8.0),
+    (50.0, 25.0, 200.0, 81.0 / 16.0),
+]
+
+
+@pytest.mark.parametrize("cv,ei,ej,gam", UNEQUAL_T)
+def test_ser_hand_case_unequal_temperatures(ora, cv, ei, ej, gam):
+    # chi = 1/4, v_ij = 1, dt = 0.01: dp_ij = -gamma / 400; every term of
+    # Eq. (SER_eint_discretization) is exact in binary for these gammas:
+    # Delta eps_i = Delta eps_j = -1/2 dp_ij (1 + dp_ij)
+    q, p, _ = two_particles()
+    eps = np.array([ei, ej])
+    rep = ora.make_replica(2, (4.0, 4.0, 4.0), cv)
+    prm = ora.make_params(sigma=3.0, noise=False)
+    p1, e1 = ora.fd(rep, 0, prm, q, p, eps, 0, 0.01, "SER")
+    dp = -gam / 400.0
+    expect_p = {27.0 / 8.0: 0.4915625, 81.0 / 16.0: 0.48734375}[gam]
+    expect_de = {27.0 / 8.0: 0.004183154296875, 81.0 / 16.0: 0.00624803466796875}[gam]
+    assert 0.5 + dp == expect_p
+    assert np.allclose(p1, [[expect_p, 0, 0], [-expect_p, 0, 0]], atol=1e-15, rtol=0)
+    assert np.allclose(e1 - eps, [expect_de, expect_de], atol=3e-14, rtol=0)
+
+
+@pytest.mark.parametrize("cv,ei,ej,gam", UNEQUAL_T)
+def test_ssa_hand_case_unequal_temperatures(ora, cv, ei, ej, gam):
+    # a = 2 gamma chi dt / m = gamma / 200 (0.016875 and 0.0253125)
+    q, p, _ = two_particles()
+    eps = np.array([ei, ej])
+    rep = ora.make_replica(2, (4.0, 4.0, 4.0), cv)
+    prm = ora.make_params(sigma=3.0, noise=False)
+    p1, e1 = ora.fd(rep, 0, prm, q, p, eps, 0, 0.01, "SSA")
+    a = {27.0 / 8.0: 0.016875, 81.0 / 16.0: 0.0253125}[gam]
+    delta = 0.5 * math.expm1(-a)
+    assert p1[0, 0] == pytest.approx(0.5 + delta, abs=1e-15)
+    assert p1[1, 0] == pytest.approx(-0.5 - delta, abs=1e-15)
+    dK = (0.5 + delta) ** 2 - 0.25
+    assert np.allclose(e1 - eps, [-dK / 2, -dK / 2], atol=3e-14, rtol=0)
+
+
+@pytest.mark.parametrize("cv,ei,ej,gam", UNEQUAL_T)
+def test_sem_hand_case_unequal_temperatures(ora, cv, ei, ej, gam):
+    # Eq. (SEM_fd), G = 0: Delta eps = 1/2 (gamma - 27) / 400 for both
+    # (-0.02953125 and -0.027421875)
+    q, p, _ = two_particles()
+    eps = np.array([ei, ej])
+    rep = ora.make_replica(2, (4.0, 4.0, 4.0), cv)
+    prm = ora.make_params(sigma=3.0, noise=False)
+    p1, e1 = ora.fd(rep, 0, prm, q, p, eps, 0, 0.01, "SEM")
+    expect = {27.0 / 8.0: -0.02953125, 81.0 / 16.0: -0.027421875}[gam]
+    assert np.allclose(e1 - eps, [expect, expect], atol=3e-14, rtol=0)
+
+
 def test_sem_hand_case(ora):
     # Eq. (SEM_fd) with G = 0: Delta eps_i = 1/2 (gamma v_ij^2 - d sigma^2/m) chi dt
     #   = 0.5 * (4.5 - 27) * 0.25 * 0.01 = -0.028125
