@@ -133,8 +133,8 @@ def workload_and_scheme(args):
 # Lane operations per unique pair (counted from the kernels' formulas; see
 # the roofline section of the design notes): one Gaussian triple = Philox4x32-10
 # (~80 INT) + Box-Muller (~100: 2 log, 2 sqrt, sincospi, cospi, scaling);
-# SSA pair map ~130 (2 expm1, 1 div, 1 sqrt, momenta, dK, two compensated eps
-# updates, two beta divisions); SER sweep 1 ~40, sweep 2 ~55 pair arithmetic.
+# SSA pair map ~95 (one expm1, one rsqrt, momenta, dK, two compensated eps
+# updates, two fast beta divisions); SER sweep 1 ~40, sweep 2 ~55 pair arithmetic.
 OPS_GAUSS = 180.0
 OPS_PER_PAIR = {"ssa": 95.0, "ssa_gauss": OPS_GAUSS, "sweep1": OPS_GAUSS + 40.0, "sweep2": OPS_GAUSS + 55.0}
 KERNEL_OF_PHASE = {"ssa": "k_ssa_colour", "ssa_gauss": "k_ssa_gauss", "sweep1": "k_ser_sweep1",
@@ -452,7 +452,9 @@ def _gpu_vs_oracle(sub, q, p, e, ref, nsteps, scheme, precision):
     L = np.asarray(spec.box, float)
     dq = qg - ref.q
     dq -= L * np.round(dq / L)
-    return max(float(np.max(np.abs(dq)) / np.max(np.abs(ref.q))), _rel(pg, ref.p), _rel(eg, ref.eps))
+    moved = ref.q - q                      # the oracle's displacement from the start (minimum image)
+    moved -= L * np.round(moved / L)
+    return max(float(np.max(np.abs(dq)) / np.max(np.abs(moved))), _rel(pg, ref.p), _rel(eg, ref.eps))
 
 
 def parity_report(w, base, scheme):

@@ -234,7 +234,9 @@ int dpde_create(const dpde_params* params, int32_t n_replicas,
 /* Sets the state of every replica and resets the step counter to `step`.
  *  q, p     : 3*N doubles, particle-major (x,y,z), replicas concatenated in
  *             order, ids = index within the replica's segment. q is wrapped
- *             into the box. In DPDE_MIXED mode q, p are rounded to float.
+ *             into the box along periodic axes; along the z axis of a walled
+ *             replica it is kept as given (z = L_z stays on the upper face).
+ *             In DPDE_MIXED mode q, p are rounded to float.
  *  eps      : N doubles.
  *  on_device: 0 = host pointers, 1 = device pointers (e.g. torch data_ptr()).
  * Computes the forces F(q) of the new state. Synchronous. */
@@ -242,7 +244,8 @@ int dpde_set_state(dpde_handle* h, const double* q, const double* p,
                    const double* eps, int64_t step, int32_t on_device);
 
 /* Copies the state out in id order (same layout as dpde_set_state); q in
- * [0, L). Any of q, p, eps may be NULL. Synchronous; returns the device
+ * [0, L) along periodic axes, between the walls along a walled z. Any of q,
+ * p, eps may be NULL. Synchronous; returns the device
  * status (DPDE_ERR_NEG_EPS / DPDE_ERR_NONFINITE) raised since the last check. */
 int dpde_get_state(dpde_handle* h, double* q, double* p, double* eps,
                    int32_t on_device);
@@ -296,26 +299,31 @@ const char* dpde_last_error(const dpde_handle* h);
 
 /* Observables of one system (the quantities of dpde_observables, computed
  * in double) from a state the caller holds in device memory, without any
- * device allocation -- for callers that cannot call cudaMalloc: code that
- * runs while a stream is being captured into a CUDA graph, plug-ins inside
- * a host framework that owns all device memory, processes under a hard
- * device-memory cap. The paper has no counterpart; this is a service entry
+ * device allocation -- for callers that cannot call cudaMalloc: plug-ins
+ * inside a host framework that owns all device memory through its own pool,
+ * processes under a hard device-memory cap or with a no-allocation rule
+ * after start-up. The paper has no counterpart; this is a service entry
  * point of the library, not part of the method.
  *  params  : m, r_cut, a of the system (sigma, seed, precision unused).
  *  replica : n <= DPDE_NOALLOC_MAX_N, box with floor(L_d / r_cut) >= 3 and
  *            prod_d floor(L_d / r_cut) <= DPDE_NOALLOC_MAX_CELLS, C_v
  *            (bricks unused). Larger systems: DPDE_ERR_ARG with a message
  *            from dpde_noalloc_last_error().
- *  q, p    : 3n doubles each, eps: n doubles -- DEVICE pointers (read only).
+ *  q, p    : 3n doubles each, eps: n doubles -- DEVICE (or managed) pointers
+ *            on the current device, read only; a host pointer or memory of
+ *            another device is refused with DPDE_ERR_ARG before any launch.
+ *            Along the z axis of a walled replica positions are not wrapped
+ *            (z = 0 and z = L_z belong to the bottom and top cell layers).
  *  stream  : cudaStream_t to run on (NULL = legacy default stream).
  *  out     : one dpde_obs, host memory (out->step is 0).
  * All working memory is the library's fixed device scratch array; the call
  * clears the parts that must start at zero. The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) once for that device:
  * make it before any stream capture. Every call shares the array, so calls
- * whose work overlaps on a GPU race; callers serialise them. Synchronous on
- * `stream`. Returns DPDE_ERR_NEG_EPS / DPDE_ERR_NONFINITE like
- * dpde_observables (out is still filled). */
+ * whose work overlaps on a GPU race; callers serialise them. The call waits
+ * for `stream` before returning. Returns DPDE_ERR_NEG_EPS / DPDE_ERR_NONFINITE
+ * like dpde_observables (out is still filled; a pair with a non-finite
+ * separation is skipped, as in the handle's pair search). */
 int dpde_observables_noalloc(const dpde_params* params, const dpde_replica* replica,
                              const double* q, const double* p, const double* eps,
                              void* stream, dpde_obs* out);

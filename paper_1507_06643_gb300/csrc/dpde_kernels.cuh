@@ -155,7 +155,8 @@ __global__ void k_load_state(Ctx<T> C, const double* __restrict__ q, const doubl
     T o[3];
     for (int d = 0; d < 3; ++d) {
         double x = q[3 * s + d];
-        if (!(x >= 0.0 && x < R.L[d])) {   // wrap only what lies outside [0, L) (FP64 division is slow)
+        const bool wall = d == 2 && R.walls;   // a walled z is not periodic: z = L_z stays on the top face
+        if (!wall && !(x >= 0.0 && x < R.L[d])) {   // wrap only what lies outside [0, L) (FP64 division is slow)
             x -= R.L[d] * floor(x / R.L[d]);
             if (x >= R.L[d]) x -= R.L[d];
         }
@@ -200,8 +201,10 @@ __global__ void k_get_state(Ctx<T> C, const int* __restrict__ slot_of, double* _
         const double od[3] = {(double)qv.x, (double)qv.y, (double)qv.z};
         for (int d = 0; d < 3; ++d) {
             double x = (double)cd[d] * R.ell[d] + od[d];
-            if (x >= R.L[d]) x -= R.L[d];
-            else if (x < 0.0) x += R.L[d];
+            if (!(d == 2 && R.walls)) {   // a walled z is not periodic
+                if (x >= R.L[d]) x -= R.L[d];
+                else if (x < 0.0) x += R.L[d];
+            }
             q[3 * (size_t)g + d] = x;
         }
     }

@@ -1,15 +1,18 @@
 // dpde_noalloc.cu -- observables of one system without any device allocation.
 //
-// For callers that cannot call cudaMalloc: code running while a CUDA stream
-// is being captured into a graph (allocation calls are not allowed there),
-// plug-ins living inside a host framework that owns all device memory and
-// forbids side allocations, and processes under a hard device-memory cap.
-// The caller passes the state (device arrays) and receives the observables;
-// all working memory comes from one file-scope device array of fixed size
-// (NOALLOC_SCRATCH_BYTES, held by every GPU that loads the library until the
-// process exits). Every call shares that array: calls that overlap on the
-// GPU (different streams, threads or devices' concurrent use of the same
-// device) race and must be serialised by the caller.
+// For callers that cannot call cudaMalloc: plug-ins living inside a host
+// framework that owns all device memory through its own pool (a side
+// allocation would fail, or fragment and outgrow the pool's budget), and
+// processes under a hard device-memory cap or with a no-allocation rule after
+// start-up. The caller passes the state (device arrays) and receives the
+// observables; all working memory comes from one file-scope device array of
+// fixed size (SCRATCH_BYTES below, held by every GPU that loads the library
+// until the process exits). Every call shares that array: calls that overlap
+// on the GPU (different streams or threads using the same device) race and
+// must be serialised by the caller. The first call on a device looks up the
+// array's device address with cudaGetSymbolAddress (set-up); that first call
+// should come before any stream capture begins. Each call waits for its
+// stream before returning, to hand back the results.
 #include "dpde.h"
 #include "dpde_device.cuh"
 
@@ -60,11 +63,15 @@ struct NaGeom {
     dpde::PotT<double> pot;
 };
 
+// Cell coordinate along axis d: periodic axes wrap x into [0, L); the z axis
+// of a walled replica does not wrap (a particle on the upper wall face, z =
+// L_z, belongs to the top cell layer, one at z = 0 to the bottom one).
 __device__ __forceinline__ int na_cell(const NaGeom& G, const double* q, int i, int d) {
     double x = q[3 * i + d];
-    x -= G.L[d] * floor(x / G.L[d]);
-    int c = (int)(x * G.s[d]);
-    return c > G.nc[d] - 1 ? G.nc[d] - 1 : (c < 0 ? 0 : c);
+    if (!(d == 2 && G.walls)) x -= G.L[d] * floor(x / G.L[d]);
+    const double f = floor(x * G.s[d]);
+    if (!(f >= 0.0)) return 0;
+    return f >= (double)(G.nc[d] - 1) ? G.nc[d] - 1 : (int)f;
 }
 
 __device__ __forceinline__ int na_lin(const NaGeom& G, int cx, int cy, int cz) {
@@ -153,7 +160,7 @@ __global__ void k_na_terms(NaGeom G, const double* __restrict__ q, const double*
                             d[a] = v;
                             r2 += v * v;
                         }
-                        if (r2 >= G.rc2) continue;
+                        if (!(r2 < G.rc2)) continue;   // also drops a NaN separation
                         if (r2 > 0.0) {
                             double v, fr, lp;
                             dpde::pair_pot(G.pot, r2, 1.0 / sqrt(r2), v, fr, lp);
@@ -190,6 +197,26 @@ __global__ void k_na_final(const double* __restrict__ partial, double* __restric
 int na_fail(int code, const std::string& msg) {
     g_na_error = msg;
     return code;
+}
+
+// A state pointer must be device (or managed) memory reachable from the
+// current device: a host pointer given to the kernels would fault, or on a
+// system where the GPU can read host memory silently read the wrong data.
+int na_check_device_ptr(const void* ptr, int dev, const char* name) {
+    cudaPointerAttributes a{};
+    const cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // the failed query is not sticky: clear it
+        return na_fail(DPDE_ERR_ARG, std::string(name) + " is not a CUDA device pointer (" +
+                                         cudaGetErrorString(e) + ")");
+    }
+    if (a.type == cudaMemoryTypeManaged) return DPDE_OK;
+    if (a.type != cudaMemoryTypeDevice)
+        return na_fail(DPDE_ERR_ARG, std::string(name) + " must point to device memory (got a host pointer)");
+    if (a.device != dev)
+        return na_fail(DPDE_ERR_ARG, std::string(name) + " lives on device " + std::to_string(a.device) +
+                                         ", not on the current device " + std::to_string(dev));
+    return DPDE_OK;
 }
 
 }  // namespace
@@ -239,6 +266,14 @@ int dpde_observables_noalloc(const dpde_params* params, const dpde_replica* repl
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return na_fail(DPDE_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= NA_MAX_DEVICES) return na_fail(DPDE_ERR_ARG, "device index out of range");
+    if (G.n > 0) {
+        const void* ptrs[3] = {q, p, eps};
+        const char* names[3] = {"q", "p", "eps"};
+        for (int k = 0; k < 3; ++k) {
+            const int rc = na_check_device_ptr(ptrs[k], dev, names[k]);
+            if (rc != DPDE_OK) return rc;
+        }
+    }
     unsigned char* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_na_mutex);

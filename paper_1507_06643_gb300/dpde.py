@@ -26,6 +26,7 @@ DPDE_ERR_TIMEOUT = -6
 DPDE_ERR_CAPACITY = -7
 
 FP64, MIXED = 0, 1
+DPDE_NOALLOC_MAX_N = 262144   # particle limit of dpde_observables_noalloc (dpde.h)
 SER, HYBRID, SEM, SSA = 0, 1, 2, 3
 SCHEMES = {"SER": SER, "HYBRID": HYBRID, "SEM": SEM, "SSA": SSA}
 PRECISIONS = {"fp64": FP64, "mixed": MIXED}
@@ -227,9 +228,28 @@ def dpde_observables(h, n_replicas):
     return rc, [o.as_dict() for o in out]
 
 
+def _noalloc_arg(x, numel: int, name: str):
+    """A state argument of dpde_observables_noalloc: a contiguous float64 CUDA
+    tensor with at least `numel` elements (the C side also refuses host
+    pointers)."""
+    if x is None or not hasattr(x, "is_cuda"):
+        raise DPDEError(DPDE_ERR_ARG, f"{name} must be a CUDA tensor (got {type(x).__name__})")
+    import torch
+    if not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous() or x.numel() < numel:
+        raise DPDEError(DPDE_ERR_ARG, f"{name} must be a contiguous float64 CUDA tensor of at least "
+                                      f"{numel} elements (got {x.dtype}, {tuple(x.shape)}, device {x.device})")
+    return x
+
+
 def dpde_observables_noalloc(params: dpde_params, replica: dpde_replica, q, p, eps, stream=None):
-    """Observables of one system from device arrays (torch CUDA tensors or raw
-    device pointers), computed without any device allocation."""
+    """Observables of one system from device arrays (contiguous float64 torch
+    CUDA tensors: q and p of 3n elements, eps of n), computed without any
+    device allocation."""
+    n = int(replica.n)
+    if 0 < n <= DPDE_NOALLOC_MAX_N:
+        q = _noalloc_arg(q, 3 * n, "q")
+        p = _noalloc_arg(p, 3 * n, "p")
+        eps = _noalloc_arg(eps, n, "eps")
     out = dpde_obs()
     rc = lib().dpde_observables_noalloc(C.byref(params), C.byref(replica), _addr(q), _addr(p), _addr(eps),
                                         C.c_void_p(stream) if stream else None, C.byref(out))

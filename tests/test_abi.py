@@ -105,3 +105,10 @@ def test_oracle_struct_layouts_match_its_header(tmp_path):
         assert got[(name, "size")] == C.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def test_noalloc_limit_matches_the_header():
+    from paper_1507_06643_gb300 import dpde
+    text = open(os.path.join(ROOT, "include", "dpde.h")).read()
+    m = re.search(r"#define DPDE_NOALLOC_MAX_N\s+(\d+)", text)
+    assert m and int(m.group(1)) == dpde.DPDE_NOALLOC_MAX_N
