@@ -216,10 +216,16 @@ class System:
             self.F[s] = forces(self.reps[r], prm, self.q[s])
 
     def _wrap(self, r):
+        """Periodic axes into [0, L); the z axis of a replica closed by walls
+        (Sec. V: no periodicity along the shock axis) is left as given, so a
+        particle on the upper wall face z = L_z stays there."""
         s = slice(self.offsets[r], self.offsets[r + 1])
         box = np.array(self.reps[r].box[:])
-        self.q[s] = np.mod(self.q[s], box)
-        self.q[s] = np.where(self.q[s] >= box, self.q[s] - box, self.q[s])
+        axes = [0, 1] if self.reps[r].walls else [0, 1, 2]
+        q = self.q[s]
+        q[:, axes] = np.mod(q[:, axes], box[axes])
+        q[:, axes] = np.where(q[:, axes] >= box[axes], q[:, axes] - box[axes], q[:, axes])
+        self.q[s] = q
 
     projection = None   # per-replica E0 when the projection of Sec. IV.C is on
 

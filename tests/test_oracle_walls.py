@@ -89,6 +89,32 @@ def test_no_pair_across_the_walls(ora):
     assert np.allclose(F[0], -F[2]) and F[0, 0] < 0
 
 
+def test_particles_on_the_wall_faces_stay_there(ora):
+    """A particle on the upper wall face z = L_z is not wrapped to z = 0 (the
+    walled z axis has no periodic image): it keeps its position in the
+    System, and the potential energy equals a brute-force sum with the
+    minimum image along x and y only."""
+    n, box = 400, (5.0, 5.0, 6.2)
+    q, p, e = state(n, box, 51)
+    q[:20, 2] = 0.0
+    q[20:40, 2] = box[2]
+    q[40:60, 2] = box[2] - 1e-12      # within 1e-12 of the face-bound ones' plane
+    S = ora.System([ora.make_replica(n, box, 100.0, walls=1)], ora.make_params(), q, p, e)
+    assert np.array_equal(S.q, q)
+    L = np.asarray(box)
+    U = 0.0
+    for i in range(n):
+        d = q[i] - q[i + 1:]
+        d[:, :2] -= L[:2] * np.round(d[:, :2] / L[:2])
+        r = np.sqrt((d * d).sum(axis=1))
+        U += (12.5 * (1 - r[r < 1.0]) ** 2).sum()
+    assert S.observables()["U"] == pytest.approx(U, rel=1e-12)
+    # the periodic reading would wrap the face particles onto z = 0
+    P = ora.System([ora.make_replica(n, box, 100.0)], ora.make_params(), q, p, e)
+    assert np.all(P.q[20:40, 2] == 0.0)
+    assert abs(P.observables()["U"] - U) > 1.0
+
+
 @pytest.mark.parametrize("n,box,bricks", [(64, (3.3, 6.9, 9.9), (1, 2, 3)), (1000, (6.934,) * 3, (2, 2, 2)),
                                           (600, (5.0, 5.0, 8.1), (1, 1, 1))])
 def test_pairs_with_walls_brute_cells_kdtree(ora, n, box, bricks):
