@@ -278,6 +278,8 @@ def run_ours(args):
     kernel = KERNEL_OF_PHASE.get(dom, dom)
     if dom == "ssa" and args.scheme == "HYBRID" and tuning.get("ssa_mode") == 1:
         kernel = "k_ssa_domains"
+    if tuning.get("ssa_mode") == 2 and dom in ("ssa", "ssa_gauss"):
+        kernel = {"ssa": "k_ssa_exec", "ssa_gauss": "k_ssa_sched"}[dom]
     traffic = MEASURED_TRAFFIC.get((w.name, args.scheme, w.precision, kernel))
     if args.bricks:
         traffic = None

@@ -342,7 +342,10 @@ const char* dpde_noalloc_last_error(void);
 #define DPDE_PHASE_SWEEP1      5  /* SER first sweep                       */
 #define DPDE_PHASE_SWEEP2      6  /* SER second sweep / SEM sweep / copy   */
 #define DPDE_PHASE_OTHER       7  /* projection on the internal energies   */
-#define DPDE_PHASE_SSA_GAUSS   8  /* Gaussians of the SSA pairs            */
+#define DPDE_PHASE_SSA_GAUSS   8  /* SSA preparation: the pairs' Gaussians  */
+                                  /* (ssa_mode 0, 1) or the level schedule  */
+                                  /* (ssa_mode 2, whose execution draws the */
+                                  /* Gaussians itself)                       */
 #define DPDE_NUM_PHASES        9
 
 /* Runs n steps like dpde_step without a graph, with CUDA events recorded on
@@ -375,16 +378,22 @@ typedef struct dpde_tuning {
     int32_t tile_edge;   /* force tile edge in cells, 2..8 (default 6)                */
     int32_t block;       /* threads per block of the per-particle kernels: a multiple  */
                          /* of 32 in 64..1024 (default 256)                           */
-    int32_t ssa_block;   /* threads per block of the per-class SSA launches: 32, 64,   */
-                         /* 96 or 128 (the per-domain form runs one warp per block)    */
-                         /* (default 64)                                               */
-    int32_t ssa_mode;    /* form of the SSA launches; both give the same results bit  */
-                         /* for bit. 0 (default): one launch per colour class, a      */
-                         /* thread per cell; 1 (Hybrid only, DPDE_SSA then takes 0):  */
-                         /* one launch in which each warp takes whole domains and     */
-                         /* walks their colour classes in order (domains share no     */
-                         /* chain, so their sequences commute), the domains' state    */
-                         /* staged in shared memory where it fits                     */
+    int32_t ssa_block;   /* threads per block of the per-class SSA launches and of the */
+                         /* level form's execution: 32, 64, 96 or 128 (the per-domain  */
+                         /* form runs one warp per block) (default 64)                */
+    int32_t ssa_mode;    /* form of the SSA launches; all give the same results bit   */
+                         /* for bit. 2 (default): by dependency levels -- per domain, */
+                         /* every map of the sequence gets the level 1 + the larger   */
+                         /* level of the last earlier maps of its two particles; a    */
+                         /* block per domain runs the levels in order from shared     */
+                         /* memory (maps of one level share no particle); used where  */
+                         /* no domain is expected above 16,384 particles, else 0.     */
+                         /* 0: one launch per colour class, a thread per cell;        */
+                         /* 1 (Hybrid only, DPDE_SSA then takes 0): one launch in     */
+                         /* which each warp takes whole domains and walks their       */
+                         /* colour classes in order (domains share no chain, so their */
+                         /* sequences commute), the domains' state staged in shared   */
+                         /* memory where it fits                                      */
     int32_t ssa_group;   /* domains per warp of ssa_mode 1, 1..8; 0 = automatic (32 /  */
                          /* the most cells of one class in one domain); get_tuning     */
                          /* reports the value in use                                   */
@@ -402,8 +411,8 @@ int dpde_set_tuning(dpde_handle* h, const dpde_tuning* t);
 
 /* Autotuner: times `steps` graph-replayed steps of `scheme` at `dt` (after
  * one untimed replay) for each candidate -- tile edges 4..8, then per-particle block sizes
- * 128, 256, 512, then SSA block sizes 32, 64, 128, then the SSA modes 1 and
- * 0, then (Hybrid in ssa_mode 1) 1..4 domains per warp, each stage keeping the
+ * 128, 256, 512, then SSA block sizes 32, 64, 128, then the SSA modes 2, 1
+ * and 0, then (Hybrid in ssa_mode 1) 1..4 domains per warp, each stage keeping the
  * best so far, a candidate replacing it only when more than 1% faster -- on
  * the handle's current state, restoring that state, its
  * forces and its step counter after every trial; then applies the fastest
@@ -414,9 +423,10 @@ int dpde_autotune(dpde_handle* h, int32_t scheme, double dt, int32_t steps, dpde
 /* Number of kernel launches in one step of `scheme` (the kernel nodes of
  * the step's CUDA graph, captured here without being run; *launches, host
  * pointer). The count depends on the handle's geometry and tuning: the SSA
- * part has one launch drawing the Gaussians, then one per non-empty cell
- * colour class (ssa_mode 0, or DPDE_SSA) or one for all domains (Hybrid in
- * ssa_mode 1). No device work; the handle's state and step counter are
+ * part has two schedule and two execution launches (ssa_mode 2), or one
+ * launch drawing the Gaussians, then one per non-empty cell colour class
+ * (ssa_mode 0, or DPDE_SSA in modes 1 and 2 without the level form) or one
+ * for all domains (Hybrid in ssa_mode 1). No device work; the handle's state and step counter are
  * unchanged. DPDE_ERR_ARG for a bad scheme. */
 int dpde_step_launches(dpde_handle* h, int32_t scheme, int64_t* launches);
 

@@ -1,7 +1,7 @@
 // dpde_api.cu -- the C ABI of include/dpde.h: handle, buffers, launch
 // sequence of one timestep, CUDA-graph replay, observables, diagnostics.
 #include "dpde.h"
-#include "dpde_kernels.cuh"
+#include "dpde_ssa_levels.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -70,9 +70,21 @@ struct dpde_handle {
     int* dom_off = nullptr;
     int* dom_cell0 = nullptr;    // first cell of each brick, then ncells
     double dom_mean = 0.0;       // most particles per brick of a replica, on average
-    int ssa_mode = 0;
+    int ssa_mode = 2;
     bool any_walls = false;       // some replica has walls along z
     WallPos* wallpos = nullptr;   // upper wall of each replica for the step's drift
+    // SSA by dependency levels (ssa_mode 2): domain tables of whole replicas
+    // (DPDE_SSA; the bricks' are dom_*), per-domain level offsets and counts,
+    // the deferred-domain lists ([0] schedule count, [1] execution count,
+    // then the two lists), and the shared-memory capacities per table
+    int *rdom_cells = nullptr, *rdom_off = nullptr, *rdom_cell0 = nullptr;
+    int *lv_off = nullptr, *lv_n = nullptr, *ssa_defer = nullptr;
+    int ndom_max = 1;
+    struct SsaCaps {
+        int scap_s = 0, ecap_s = 0, scap_sd = 0, ecap_sd = 0, scap_x = 0, scap_xd = 0;
+        bool ok = false;   // domains small enough for the level form
+    } ssa_caps[2];
+    int nsm = 152;
     int ssa_group = 0;        // bricks per warp; 0 = dom_group_auto
     int dom_group_auto = 1;   // 32 / the largest class of a brick, in 1..SSA_GROUP_MAX
     int hcap = 0;             // halo particles staged per force tile
@@ -152,6 +164,13 @@ Ctx<T> make_ctx(dpde_handle* h) {
     return C;
 }
 
+// The level form's records live in the buffer of the forward entries'
+// Gaussians (unused by that form): N * cap 32-bit (s, t) words, then, from a
+// 256-byte boundary, N * cap weights.
+size_t ssa_rec_w_offset(const dpde_handle* h) {
+    return ((size_t)std::max(1, h->N) * (size_t)h->nbr_cap * sizeof(uint32_t) + 255) & ~(size_t)255;
+}
+
 // phase markers (only when dpde_step_profiled is running)
 void phase(dpde_handle* h, cudaStream_t st, int ph, int end) {
     if (!h->profiling) return;
@@ -202,8 +221,44 @@ void enqueue_force(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T half_dt, 
 // brick domains (Hybrid, ssa_mode 1), one launch in which each warp walks the
 // colour classes of whole bricks, or one launch per non-empty colour class,
 // in colour order; both apply the same sequence.
+// The SSA sequence by dependency levels (ssa_mode 2): the schedule of every
+// domain, then its execution; each kernel's regular launch (one block per
+// domain) defers domains beyond its shared-memory capacities to a second,
+// persistent launch with larger ones.
+template <class T>
+void enqueue_ssa_levels(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_dt, int whole) {
+    const dpde_handle::SsaCaps& K = h->ssa_caps[whole];
+    const SsaDomains D = whole ? SsaDomains{h->rdom_cells, h->rdom_off, h->rdom_cell0, h->R}
+                               : SsaDomains{h->dom_cells, h->dom_off, h->dom_cell0, h->nbricks};
+    SsaLevels<T> V;
+    V.lv_off = h->lv_off;
+    V.lv_n = h->lv_n;
+    V.rec_st = reinterpret_cast<uint32_t*>(h->fwd_g);
+    V.rec_w = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(h->fwd_g) + ssa_rec_w_offset(h));
+    int* cnt = h->ssa_defer;
+    int* sdef = cnt + 2;
+    int* xdef = sdef + h->ndom_max;
+    cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st);
+    phase(h, st, DPDE_PHASE_SSA_GAUSS, 0);
+    k_ssa_sched<T><<<D.n, SCHED_THREADS, ssa_sched_smem(K.scap_s, K.ecap_s), st>>>(C, D, V, K.scap_s, K.ecap_s,
+                                                                                  nullptr, nullptr, sdef, cnt);
+    k_ssa_sched<T><<<h->nsm, SCHED_THREADS, ssa_sched_smem(K.scap_sd, K.ecap_sd), st>>>(
+        C, D, V, K.scap_sd, K.ecap_sd, sdef, cnt, nullptr, nullptr);
+    phase(h, st, DPDE_PHASE_SSA_GAUSS, 1);
+    phase(h, st, DPDE_PHASE_SSA, 0);
+    k_ssa_exec<T><<<D.n, h->ssa_block, ssa_exec_smem<T>(K.scap_x), st>>>(C, D, V, K.scap_x, nullptr, nullptr, xdef,
+                                                                         cnt + 1, dt, sqrt_dt);
+    k_ssa_exec<T><<<h->nsm, h->ssa_block, ssa_exec_smem<T>(K.scap_xd), st>>>(C, D, V, K.scap_xd, xdef, cnt + 1,
+                                                                             nullptr, nullptr, dt, sqrt_dt);
+    phase(h, st, DPDE_PHASE_SSA, 1);
+}
+
 template <class T>
 void enqueue_ssa(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_dt, int whole) {
+    if (h->ssa_mode == 2 && h->ssa_caps[whole].ok) {
+        enqueue_ssa_levels<T>(h, C, st, dt, sqrt_dt, whole);
+        return;
+    }
     const std::vector<int>& off = h->col_off[whole];
     phase(h, st, DPDE_PHASE_SSA_GAUSS, 0);
     k_ssa_gauss<T><<<ceil_div(h->N, 256), 256, 0, st>>>(C);
@@ -386,7 +441,7 @@ void free_all(dpde_handle* h) {
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
     void* bufs[] = {h->qA, h->pA, h->qB, h->pB, h->F, h->dp, h->upot, h->proj_e0, h->proj_shift, h->proj_partial, h->eA, h->eB, h->nbr_w, h->cA, h->cB, h->nbr_j,
-                    h->nbr_n, h->fwd_j, h->fwd_w, h->fwd_g, h->fwd_n, h->tile_org, h->tile_dim, h->defer, h->col_cells[0], h->col_cells[1], h->dom_cells, h->dom_off, h->dom_cell0, h->wallpos, h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
+                    h->nbr_n, h->fwd_j, h->fwd_w, h->fwd_g, h->fwd_n, h->tile_org, h->tile_dim, h->defer, h->col_cells[0], h->col_cells[1], h->dom_cells, h->dom_off, h->dom_cell0, h->rdom_cells, h->rdom_off, h->rdom_cell0, h->lv_off, h->lv_n, h->ssa_defer, h->wallpos, h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
                     h->rep_of_cell, h->brick_rep, h->tab, h->chunk_rep, h->chunk_begin, h->chunk_end,
                     h->rep_chunk_begin, h->partial, h->obs_out, h->d_reps, h->d_step, h->d_status,
                     h->staging, h->cells_out};
@@ -586,6 +641,7 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     // and whole replicas (m = 1)
     std::vector<int> col_cells[2];
     std::vector<unsigned char> dom_col((size_t)std::max<long long>(1, ncells), 0);
+    std::vector<unsigned char> rep_col((size_t)std::max<long long>(1, ncells), 0);
     for (int m = 0; m < 2; ++m) {
         std::vector<std::vector<int>> cls(NCOLOURS);
         for (const RepInfo& I : h->info) {
@@ -609,7 +665,7 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
                         const int k = (col[2][z] * 5 + col[1][y]) * 5 + col[0][x];
                         const int c = I.cell_off + tx[x] + ty[y] + tz[z];
                         cls[k].push_back(c);
-                        if (m == 0) dom_col[c] = (unsigned char)k;
+                        (m == 0 ? dom_col : rep_col)[c] = (unsigned char)k;
                     }
         }
         h->col_off[m].assign(1, 0);
@@ -647,6 +703,58 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     }
     dom_cell0.push_back((int)ncells);
     h->dom_group_auto = std::max(1, std::min(SSA_GROUP_MAX, 32 / class_max));
+    // the same per whole replica (the domain of DPDE_SSA)
+    std::vector<int> rdom_cells, rdom_off, rdom_cell0;
+    rdom_cells.reserve((size_t)ncells);
+    for (const RepInfo& I : h->info) {
+        int cnt[NCOLOURS + 1] = {0};
+        const int c0 = I.cell_off;
+        rdom_cell0.push_back(c0);
+        for (int c = c0; c < c0 + I.ncells; ++c) ++cnt[rep_col[c] + 1];
+        const int base = (int)rdom_cells.size();
+        rdom_off.push_back(base);
+        for (int k = 0; k < NCOLOURS; ++k) {
+            cnt[k + 1] += cnt[k];
+            rdom_off.push_back(base + cnt[k + 1]);
+        }
+        rdom_cells.resize(rdom_cells.size() + I.ncells);
+        for (int c = c0; c < c0 + I.ncells; ++c) rdom_cells[base + cnt[rep_col[c]]++] = c;
+    }
+    rdom_cell0.push_back((int)ncells);
+    // shared-memory capacities of the level form, per domain table (0 bricks,
+    // 1 whole replicas), from the mean domain size M: regular launches hold
+    // M + 5 sqrt(M) + 32 particles (a uniform fluid's domains stay below) for
+    // the execution, 1.3 M + 64 particles and 1.3 M e + 256 entries (e forward
+    // entries per particle at the densest replica's density) for the
+    // schedule; the deferred launches take what ~200 KB hold (the schedule
+    // 16,384 particles). The form is used where no domain is expected above
+    // 16,384 particles.
+    {
+        const double e_pp = 2.0 / 3.0 * M_PI * rho_max * P.r_cut * P.r_cut * P.r_cut * 1.15;
+        const size_t smem_big = 200 * 1024;
+        const size_t per = h->mixed ? (sizeof(float4) + sizeof(ff) + 4) : (sizeof(d4) + sizeof(double) + 4);
+        for (int t = 0; t < 2; ++t) {
+            dpde_handle::SsaCaps& K = h->ssa_caps[t];
+            const int ndom = t == 0 ? (int)nbricks : n_replicas;
+            double biggest = 0.0;
+            for (const RepInfo& I : h->info)
+                biggest = std::max(biggest, t == 0 ? (double)I.n / (I.B[0] * I.B[1] * I.B[2]) : (double)I.n);
+            const double M = ndom > 0 ? (double)N / ndom : 0.0;
+            auto up16 = [](double x) { return ((int)std::ceil(x) + 15) / 16 * 16; };
+            // entries that fit beside sc particles in ~200 KB of schedule
+            auto ecap_fit = [&](int sc) {
+                return std::min(SSA_LOCAL_MAX,
+                                (int)((smem_big - SSA_LV_STRIDE * sizeof(int)) / 2 - (2 * sc + 1)) / 16 * 16);
+            };
+            K.scap_s = std::min(16384, up16(1.3 * M + 64));
+            K.ecap_s = std::min(ecap_fit(K.scap_s), up16(1.3 * M * e_pp + 256));
+            K.scap_sd = 16384;
+            K.ecap_sd = ecap_fit(K.scap_sd);
+            K.scap_x = std::min((int)((smem_big - 32) / per), ((int)std::ceil(M + 5.0 * std::sqrt(M) + 32) + 31) / 32 * 32);
+            K.scap_xd = (int)((smem_big - 32) / per);
+            K.ok = biggest <= 16384.0;
+        }
+    }
     auto bail = [&](cudaError_t e, const char* what) {
         std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
         int code = e == cudaErrorMemoryAllocation ? DPDE_ERR_OOM : DPDE_ERR_CUDA;
@@ -750,6 +858,35 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         CKC(cudaMemcpy(h->dom_off, dom_off.data(), sizeof(int) * dom_off.size(), cudaMemcpyHostToDevice));
     CKC(cudaMalloc(&h->dom_cell0, sizeof(int) * dom_cell0.size()));
     CKC(cudaMemcpy(h->dom_cell0, dom_cell0.data(), sizeof(int) * dom_cell0.size(), cudaMemcpyHostToDevice));
+    CKC(cudaMalloc(&h->rdom_cells, sizeof(int) * std::max<size_t>(1, rdom_cells.size())));
+    CKC(cudaMalloc(&h->rdom_off, sizeof(int) * rdom_off.size()));
+    CKC(cudaMalloc(&h->rdom_cell0, sizeof(int) * rdom_cell0.size()));
+    if (!rdom_cells.empty())
+        CKC(cudaMemcpy(h->rdom_cells, rdom_cells.data(), sizeof(int) * rdom_cells.size(), cudaMemcpyHostToDevice));
+    CKC(cudaMemcpy(h->rdom_off, rdom_off.data(), sizeof(int) * rdom_off.size(), cudaMemcpyHostToDevice));
+    CKC(cudaMemcpy(h->rdom_cell0, rdom_cell0.data(), sizeof(int) * rdom_cell0.size(), cudaMemcpyHostToDevice));
+    h->ndom_max = std::max(1, std::max(h->nbricks, h->R));
+    CKC(cudaMalloc(&h->lv_off, sizeof(int) * (size_t)h->ndom_max * SSA_LV_STRIDE));
+    CKC(cudaMalloc(&h->lv_n, sizeof(int) * (size_t)h->ndom_max));
+    CKC(cudaMalloc(&h->ssa_defer, sizeof(int) * (2 + 2 * (size_t)h->ndom_max)));
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
+        size_t ms = 0, mx = 0;
+        for (const auto& K : h->ssa_caps) {
+            ms = std::max({ms, ssa_sched_smem(K.scap_s, K.ecap_s), ssa_sched_smem(K.scap_sd, K.ecap_sd)});
+            mx = std::max({mx, h->mixed ? ssa_exec_smem<float>(K.scap_x) : ssa_exec_smem<double>(K.scap_x),
+                           h->mixed ? ssa_exec_smem<float>(K.scap_xd) : ssa_exec_smem<double>(K.scap_xd)});
+        }
+        const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        if (h->mixed) {
+            CKC(cudaFuncSetAttribute(k_ssa_sched<float>, A, (int)ms));
+            CKC(cudaFuncSetAttribute(k_ssa_exec<float>, A, (int)mx));
+        } else {
+            CKC(cudaFuncSetAttribute(k_ssa_sched<double>, A, (int)ms));
+            CKC(cudaFuncSetAttribute(k_ssa_exec<double>, A, (int)mx));
+        }
+    }
     if (h->mixed)
         CKC(cudaFuncSetAttribute(k_ssa_domains<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SSA_DOMAIN_SMEM));
     else
@@ -895,7 +1032,7 @@ int dpde_set_tuning(dpde_handle* h, const dpde_tuning* t) {
     if (!h || !t) return DPDE_ERR_ARG;
     if (t->tile_edge < 2 || t->tile_edge > TILE_EDGE_MAX || t->block < 64 || t->block > 1024 ||
         t->block % 32 != 0 || t->ssa_block < 32 || t->ssa_block > SSA_THREADS_MAX || t->ssa_block % 32 != 0 ||
-        (t->ssa_mode != 0 && t->ssa_mode != 1) || t->ssa_group < 0 || t->ssa_group > SSA_GROUP_MAX ||
+        (t->ssa_mode < 0 || t->ssa_mode > 2) || t->ssa_group < 0 || t->ssa_group > SSA_GROUP_MAX ||
         t->reserved != 0)
         return fail(h, DPDE_ERR_ARG, "tuning out of range");
     CK(h, cudaStreamSynchronize(h->stream));
@@ -981,9 +1118,9 @@ int dpde_autotune(dpde_handle* h, int32_t scheme, double dt, int32_t steps, dpde
         double best_ms = 0.0;
         if ((rc = trial(best, best_ms)) != DPDE_OK) break;
         const int edges[] = {4, 5, 6, 7, 8}, blocks[] = {128, 256, 512}, ssa_blocks[] = {32, 64, 128},
-                  modes[] = {1, 0}, groups[] = {1, 2, 3, 4};
+                  modes[] = {2, 1, 0}, groups[] = {1, 2, 3, 4};
         const int* cands[] = {edges, blocks, ssa_blocks, modes, groups};
-        const int ncands[] = {5, 3, 3, 2, 4};
+        const int ncands[] = {5, 3, 3, 3, 4};
         for (int stage = 0; stage < 5 && rc == DPDE_OK; ++stage) {
             // bricks per warp matter only to the per-brick SSA launch
             if (stage == 4 && (best.ssa_mode != 1 || scheme != DPDE_HYBRID)) break;

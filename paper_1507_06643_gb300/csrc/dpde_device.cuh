@@ -60,6 +60,32 @@ __device__ __forceinline__ ff ff_add(ff a, float b) {
     const float hi = __fadd_rn(s, lo);
     return {hi, __fsub_rn(lo, __fsub_rn(hi, s))};
 }
+// Knuth's two-sum: a + b = s + err exactly
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+// compensated pair + compensated pair (normalised)
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    float e;
+    const float s = two_sum(a.hi, b.hi, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float hi = __fadd_rn(s, e);
+    return {hi, __fsub_rn(e, __fsub_rn(hi, s))};
+}
+// (p1 - p0)(p1 + p0) of two floats as hi + lo, to a few units of 2^-46 of
+// its size: both factors by two-sum, their leading product by the FMA
+// two-product (its rounding error exactly), the cross terms in float.
+__device__ __forceinline__ float diff_of_squares(float p1, float p0, float& lo) {
+    float ea, eb;
+    const float a = two_sum(p1, -p0, ea);
+    const float b = two_sum(p1, p0, eb);
+    const float h = __fmul_rn(a, b);
+    lo = __fadd_rn(__fmaf_rn(a, b, -h), __fadd_rn(__fmul_rn(a, eb), __fmul_rn(ea, b)));
+    return h;
+}
 __device__ __forceinline__ double eps_value(double e) { return e; }
 __device__ __forceinline__ double eps_value(ff e) { return (double)e.hi + (double)e.lo; }
 __device__ __forceinline__ void eps_from(double v, double& e) { e = v; }

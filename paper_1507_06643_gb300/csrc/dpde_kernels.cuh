@@ -924,6 +924,36 @@ __global__ void k_ser_sweep1(Ctx<T> C, T dt, T sqrt_dt) {
     C.dp[i] = out;
 }
 
+__device__ __forceinline__ double eps_half(double x) { return 0.5 * x; }
+__device__ __forceinline__ ff eps_half(ff x) { return {0.5f * x.hi, 0.5f * x.lo}; }
+
+// eps_i + add - Delta K_i, Delta K_i = (p' - p).(p' + p) / (2m) the kinetic-
+// energy change of the stored momenta p -> p'. In FP64 plain arithmetic; in
+// the mixed mode Delta K is formed as a compensated pair from exact
+// two-sums and two-products of the float momenta, so that the internal
+// energy absorbs the kinetic change to ~2^-46 relative rather than 2^-24.
+__device__ __forceinline__ double eps_minus_dk(double e, double add, const d4& pn, const d4& pi, double hm) {
+    const double dK = ((pn.x - pi.x) * (pn.x + pi.x) + (pn.y - pi.y) * (pn.y + pi.y) +
+                       (pn.z - pi.z) * (pn.z + pi.z)) * hm;
+    return e + (add - dK);
+}
+__device__ __forceinline__ ff eps_minus_dk(ff e, ff add, const float4& pn, const float4& pi, float hm) {
+    float lx, ly, lz;
+    const float hx = diff_of_squares(pn.x, pi.x, lx);
+    const float hy = diff_of_squares(pn.y, pi.y, ly);
+    const float hz = diff_of_squares(pn.z, pi.z, lz);
+    float e1, e2;
+    const float s1 = two_sum(hx, hy, e1);
+    const float s2 = two_sum(s1, hz, e2);
+    const float lo = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(lx, __fadd_rn(ly, lz)));
+    // -Delta K as a pair (hm = 1/(2m), exact for a power-of-two mass)
+    const float nh = -__fmul_rn(s2, hm), nl = -__fmul_rn(lo, hm);
+    ff d;
+    d.hi = __fadd_rn(nh, nl);
+    d.lo = __fsub_rn(nl, __fsub_rn(d.hi, nh));
+    return ff_add(ff_add(e, add), d);
+}
+
 // second sweep, Eq. (SER_eint_discretization), in the equivalent form
 //   Delta eps_i = -Delta K_i + 1/2 sum_j T_ij,
 //   T_ij = delta p_ij . (v_i + v_j + (delta p_i + delta p_j) / (2m)),
@@ -939,7 +969,7 @@ __global__ void k_ser_sweep2(Ctx<T> C, T dt, T sqrt_dt) {
     const uint32_t step = (uint32_t)*C.step;
     const T sdt = C.sigma * sqrt_dt;
     const T hm = T(0.5) * C.inv_m;
-    T tsum = 0;
+    eps_t<T> tsum{};   // compensated in the mixed mode
     for (int f0 = 0; f0 < W.total; f0 += 32) {
         const int f = f0 + W.lane;
         int o, k;
@@ -960,7 +990,7 @@ __global__ void k_ser_sweep2(Ctx<T> C, T dt, T sqrt_dt) {
         } else {
             o = 32;
         }
-        tsum += warp_owner_sum(W, f0, o, tv);
+        tsum = eps_add(tsum, warp_owner_sum(W, f0, o, tv));
     }
     if (i >= C.N) return;
     const RepInfo& R = C.reps[C.rep_of_slot[i]];
@@ -968,9 +998,7 @@ __global__ void k_ser_sweep2(Ctx<T> C, T dt, T sqrt_dt) {
     const vec_t<T> dpi = C.dp[i];
     vec_t<T> pn = pi;
     pn.x = pi.x + dpi.x; pn.y = pi.y + dpi.y; pn.z = pi.z + dpi.z;
-    const T dK = ((pn.x - pi.x) * (pn.x + pi.x) + (pn.y - pi.y) * (pn.y + pi.y) +
-                  (pn.z - pi.z) * (pn.z + pi.z)) * hm;
-    const eps_t<T> en = eps_add(C.eB[i], T(0.5) * tsum - dK);
+    const eps_t<T> en = eps_minus_dk(C.eB[i], eps_half(tsum), pn, pi, hm);
     pn.w = beta_of(en, R);
     C.qA[i] = C.qB[i];
     C.cA[i] = C.cB[i];

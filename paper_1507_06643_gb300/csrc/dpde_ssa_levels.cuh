@@ -1,0 +1,459 @@
+// dpde_ssa_levels.cuh -- the SSA sequence of every domain (Sec. III.A.2,
+// III.B.2) executed by dependency levels, domain by domain, each domain's
+// state held in shared memory.
+//
+// The SSA pair map of Eq. (SSA_ij) reads and writes the state of its two
+// particles only, so two maps on disjoint particles commute exactly: the
+// result of the sequence depends only on, for every particle, the order of
+// the maps that touch it. Give map k of the sequence the level
+//     lev(k) = 1 + max(lev of the last earlier map touching s_k,
+//                      lev of the last earlier map touching t_k)
+// (0 if none). Maps of one level touch disjoint particles, and running the
+// levels in increasing order keeps, for every particle, the sequence order
+// of its maps -- so the level-by-level execution is the sequence, bit for
+// bit. At density 3 a domain of ~700 particles has ~3,600 maps in ~100
+// levels (the per-class chains of the colour order are ~300 maps deep).
+//
+// Two kernels per step:
+//   k_ssa_sched  one block per domain: stages the domain's forward entries
+//                (partner slots, as the force pass wrote them) in shared
+//                memory, walks the colour classes in order computing every
+//                map's level (a thread per cell of the class: cells of one
+//                class share no particle), then sorts the entries by level
+//                into records (s, t, w) in global memory.
+//   k_ssa_exec   one block per domain: stages (p, eps, id) of the domain,
+//                then runs the levels in order, one thread per map, drawing
+//                each pair's Gaussian on the fly (Philox is keyed on the ids),
+//                with a block barrier between levels; writes the state back.
+// Domains too large for the regular shared-memory capacities are deferred to
+// a second launch of each kernel with larger capacities; beyond those, the
+// execution runs on the state in global memory (same levels, same bits), and
+// a domain whose schedule does not fit at all is executed class by class
+// along the colour order itself.
+#pragma once
+
+#include "dpde_kernels.cuh"
+
+namespace dpde {
+
+constexpr int SSA_MAXLEV = 1023;         // levels of one domain kept by the schedule
+constexpr int SSA_LV_STRIDE = SSA_MAXLEV + 2;
+constexpr int SCHED_THREADS = 128;
+constexpr int SSA_LOAD_BATCH = 8;       // global loads a thread keeps in flight
+constexpr int SSA_EXEC_THREADS_MAX = 128;
+constexpr int SSA_LOCAL_MAX = 65535;      // particles (and entries) of one domain: 16-bit local indices
+
+// Domains of the SSA sequence: the cells of each domain sorted by colour
+// class (`cells`), the NCOLOURS + 1 class starts of every domain in `cells`
+// (`off`), and the first cell of every domain, then the total cell count
+// (`cell0`). A domain is a contiguous cell (and slot) range.
+struct SsaDomains {
+    const int* cells;
+    const int* off;
+    const int* cell0;
+    int n;
+};
+
+// The level schedule of every domain: per domain the record offsets of its
+// levels (lv_off[d * SSA_LV_STRIDE + l], l = 0..nlev, records of level l in
+// [lv_off[l], lv_off[l + 1])), its level count (lv_n[d]; -1: no schedule,
+// executed along the colour order), and the records, domain d's at
+// [slot0(d) * cap, ...): (s_local | t_local << 16) and the weight w.
+template <class T>
+struct SsaLevels {
+    int* lv_off;
+    int* lv_n;
+    uint32_t* rec_st;
+    T* rec_w;
+};
+
+// shared bytes of k_ssa_sched for scap particles and ecap entries:
+// cnt[SSA_MAXLEV + 2] | rowoff[scap + 1] | L[scap] | ent[ecap] (16-bit)
+__host__ __device__ constexpr size_t ssa_sched_smem(int scap, int ecap) {
+    return (size_t)SSA_LV_STRIDE * sizeof(int) + (((size_t)(2 * scap + 1 + ecap) * 2 + 15) / 16) * 16;
+}
+// shared bytes of k_ssa_exec for scap staged particles: p | eps | id, after
+// up to 31 bytes that align p to 32 bytes
+template <class T>
+__host__ __device__ constexpr size_t ssa_exec_smem(int scap) {
+    return 32 + (size_t)scap * (sizeof(vec_t<T>) + sizeof(eps_t<T>) + sizeof(uint32_t));
+}
+
+// slot range [sb, se) of domain d
+template <class T>
+__device__ __forceinline__ void ssa_domain_range(const Ctx<T>& C, const SsaDomains& D, int d, int& sb, int& se) {
+    sb = C.start[D.cell0[d]];
+    se = C.start[D.cell0[d + 1]];
+}
+
+// Exclusive scan over n values v(i) held nowhere in particular: each thread
+// takes a contiguous run; writes out[i] (16-bit) for i < n and returns the
+// total. v is a callable.
+template <class F>
+__device__ __forceinline__ int block_scan_runs(int n, unsigned short* out, int* sh, F&& v) {
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int i0 = min(n, (int)threadIdx.x * per), i1 = min(n, i0 + per);
+    int run = 0;
+    for (int i = i0; i < i1; ++i) run += v(i);
+    int total;
+    int ex = block_exclusive_scan(run, sh, total);
+    for (int i = i0; i < i1; ++i) {
+        const int x = v(i);
+        out[i] = (unsigned short)ex;
+        ex += x;
+    }
+    return total;
+}
+
+// One domain's schedule on the calling block. Returns false (nothing written)
+// when the domain exceeds scap particles, ecap entries or SSA_MAXLEV levels.
+template <class T>
+__device__ bool ssa_sched_domain(const Ctx<T>& C, const SsaDomains& D, const SsaLevels<T>& V, int d, int scap,
+                                 int ecap, unsigned char* smem) {
+    __shared__ int sh[32];
+    __shared__ int s_flag, s_nlev;
+    int sb, se;
+    ssa_domain_range(C, D, d, sb, se);
+    const int nb = se - sb;
+    const int tid = threadIdx.x;
+    if (nb > scap || nb > SSA_LOCAL_MAX) return false;
+    int* cnt = reinterpret_cast<int*>(smem);
+    unsigned short* rowoff = reinterpret_cast<unsigned short*>(cnt + SSA_LV_STRIDE);
+    unsigned short* L = rowoff + scap + 1;
+    unsigned short* ent = L + scap;    // partner (local slot) of each entry, then its level
+    if (tid == 0) {
+        s_flag = 0;
+        s_nlev = 0;
+    }
+    for (int l = tid; l < SSA_LV_STRIDE; l += blockDim.x) cnt[l] = 0;
+    __syncthreads();
+    // 1. row offsets of the domain's forward entries (16-bit: checked below)
+    const int* fwd_n = C.fwd_n + sb;
+    const int E = block_scan_runs(nb, rowoff, sh, [&](int i) { return fwd_n[i]; });
+    if (E > ecap || E > SSA_LOCAL_MAX) return false;   // uniform over the block
+    if (tid == 0) rowoff[nb] = (unsigned short)E;
+    __syncthreads();   // the rows' offsets were written by other threads
+    const size_t N = (size_t)C.N;
+    // 2. partner slots, local: a thread per particle, its row's loads issued
+    //    together (entry m of particle s is at [m N + s])
+    for (int i = tid; i < nb; i += blockDim.x) {
+        L[i] = 0;
+        const int e0 = rowoff[i], nf = fwd_n[i];
+        const int* src = C.fwd_j + sb + i;
+        for (int m0 = 0; m0 < nf; m0 += SSA_LOAD_BATCH) {
+            int t[SSA_LOAD_BATCH];
+#pragma unroll
+            for (int u = 0; u < SSA_LOAD_BATCH; ++u)
+                t[u] = m0 + u < nf ? __ldg(src + (size_t)(m0 + u) * N) - sb : 0;
+#pragma unroll
+            for (int u = 0; u < SSA_LOAD_BATCH; ++u)
+                if (m0 + u < nf) {
+                    if ((unsigned)t[u] >= (unsigned)nb) s_flag = 1;   // never by construction
+                    ent[e0 + m0 + u] = (unsigned short)min(max(t[u], 0), nb - 1);
+                }
+        }
+    }
+    __syncthreads();
+    if (s_flag) {
+        if (tid == 0) flag(C.status, ST_DOMAIN);
+        return false;
+    }
+    // 3. levels, class by class (a thread per cell of the class). The
+    //    partners of one row are distinct particles, so a row is taken in
+    //    chunks: partners and their levels loaded together, the chain of
+    //    maxima run in registers, the new levels stored together.
+    const int* off = D.off + (size_t)d * (NCOLOURS + 1);
+    int mylev = 0;
+    for (int k = 0; k < NCOLOURS; ++k) {
+        const int k0 = off[k], k1 = off[k + 1];
+        if (k1 == k0) continue;   // uniform over the block
+        for (int u = k0 + tid; u < k1; u += blockDim.x) {
+            const int c = D.cells[u];
+            const int s0 = C.start[c] - sb, s1 = C.start[c + 1] - sb;
+            for (int i = s0; i < s1; ++i) {
+                int Ls = L[i];
+                const int e1 = rowoff[i + 1];
+                for (int eb = rowoff[i]; eb < e1; eb += SSA_LOAD_BATCH) {
+                    int t[SSA_LOAD_BATCH], lt[SSA_LOAD_BATCH];
+#pragma unroll
+                    for (int v = 0; v < SSA_LOAD_BATCH; ++v) t[v] = eb + v < e1 ? ent[eb + v] : 0;
+#pragma unroll
+                    for (int v = 0; v < SSA_LOAD_BATCH; ++v) lt[v] = L[t[v]];
+#pragma unroll
+                    for (int v = 0; v < SSA_LOAD_BATCH; ++v)
+                        if (eb + v < e1) {
+                            Ls = min(max(Ls, lt[v]) + 1, 65535);
+                            lt[v] = Ls;
+                        }
+#pragma unroll
+                    for (int v = 0; v < SSA_LOAD_BATCH; ++v)
+                        if (eb + v < e1) {
+                            L[t[v]] = (unsigned short)lt[v];
+                            ent[eb + v] = (unsigned short)lt[v];
+                        }
+                }
+                L[i] = (unsigned short)Ls;
+                mylev = max(mylev, Ls);
+            }
+        }
+        __syncthreads();
+    }
+    atomicMax(&s_nlev, mylev);
+    __syncthreads();
+    const int nlev = s_nlev;
+    if (nlev > SSA_MAXLEV) return false;
+    // 4. records sorted by level: counts, offsets, scatter
+    for (int e = tid; e < E; e += blockDim.x) atomicAdd(&cnt[ent[e]], 1);
+    __syncthreads();
+    if (tid < 32) {
+        // exclusive scan of cnt[1..nlev] by one warp, into cnt[1..nlev + 1]
+        int carry = 0;
+        for (int l0 = 1; l0 <= nlev + 1; l0 += 32) {
+            const int l = l0 + tid;
+            const int v = l <= nlev ? cnt[l] : 0;
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (tid >= o) x += y;
+            }
+            if (l <= nlev + 1) cnt[l] = carry + x - v;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+    __syncthreads();
+    int* lvo = V.lv_off + (size_t)d * SSA_LV_STRIDE;
+    for (int l = tid; l <= nlev; l += blockDim.x) lvo[l] = cnt[l + 1];
+    __syncthreads();
+    // the partners again from the force pass's list (just read: cached), the
+    // weights with them
+    const size_t base = (size_t)sb * C.nbr_cap;
+    for (int i = tid; i < nb; i += blockDim.x) {
+        const int e0 = rowoff[i], nf = fwd_n[i];
+        const int* srcj = C.fwd_j + sb + i;
+        const T* srcw = C.fwd_w + sb + i;
+        for (int m0 = 0; m0 < nf; m0 += SSA_LOAD_BATCH) {
+            int t[SSA_LOAD_BATCH];
+            T w[SSA_LOAD_BATCH];
+#pragma unroll
+            for (int u = 0; u < SSA_LOAD_BATCH; ++u) {
+                const bool ok = m0 + u < nf;
+                t[u] = ok ? __ldg(srcj + (size_t)(m0 + u) * N) - sb : 0;
+                w[u] = ok ? __ldg(srcw + (size_t)(m0 + u) * N) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < SSA_LOAD_BATCH; ++u)
+                if (m0 + u < nf) {
+                    const int pos = atomicAdd(&cnt[ent[e0 + m0 + u]], 1);
+                    V.rec_st[base + pos] = (uint32_t)i | ((uint32_t)min(max(t[u], 0), nb - 1) << 16);
+                    V.rec_w[base + pos] = w[u];
+                }
+        }
+    }
+    if (tid == 0) V.lv_n[d] = nlev;
+    return true;
+}
+
+// One launch over the domains: in the regular form (list == nullptr) block d
+// takes domain d and defers a domain beyond its capacities to `defer`; in the
+// dense form the blocks loop over the deferred list, and a domain beyond even
+// those capacities gets no schedule (lv_n = -1).
+template <class T>
+__global__ void __launch_bounds__(SCHED_THREADS) k_ssa_sched(Ctx<T> C, SsaDomains D, SsaLevels<T> V, int scap,
+                                                              int ecap, const int* __restrict__ list,
+                                                              const int* __restrict__ nlist, int* defer,
+                                                              int* ndefer) {
+    extern __shared__ __align__(16) unsigned char sched_smem[];
+    if (!list) {
+        const int d = blockIdx.x;
+        if (!ssa_sched_domain(C, D, V, d, scap, ecap, sched_smem) && threadIdx.x == 0) {
+            V.lv_n[d] = -1;
+            defer[atomicAdd(ndefer, 1)] = d;
+        }
+        return;
+    }
+    const int n = *nlist;
+    for (int u = blockIdx.x; u < n; u += gridDim.x) {
+        const int d = list[u];
+        if (!ssa_sched_domain(C, D, V, d, scap, ecap, sched_smem) && threadIdx.x == 0) V.lv_n[d] = -1;
+        __syncthreads();
+    }
+}
+
+// The levels of domain d on the state (P, Es, ID), indexed by local slot.
+// A thread's first map of every level (its "pass 0") runs in a three-stage
+// software pipeline: the record of level l + 2 is loaded, the Gaussian of
+// level l + 1 drawn, and the map of level l applied in the same iteration, so
+// neither the record's global-memory latency nor the Philox rounds sit between
+// two level barriers. Further maps of a crowded level follow unpipelined.
+template <class T>
+__device__ __forceinline__ void ssa_exec_levels(const Ctx<T>& C, const SsaLevels<T>& V, int d, int sb, int rep,
+                                                vec_t<T>* P, eps_t<T>* Es, const uint32_t* ID, T dt,
+                                                T sqrt_dt) {
+    const RepInfo& R = C.reps[rep];
+    const T amp0 = T(2) * C.sigma * sqrt_dt;   // amplitude of the map as gamma -> 0
+    const T k2 = T(2) * dt * C.inv_m;
+    const uint32_t step = (uint32_t)*C.step;
+    const int nlev = V.lv_n[d];
+    const int* lvo = V.lv_off + (size_t)d * SSA_LV_STRIDE;
+    const size_t base = (size_t)sb * C.nbr_cap;
+    const uint32_t* rst = V.rec_st + base;
+    const T* rw = V.rec_w + base;
+    const int tid = threadIdx.x;
+    auto apply = [&](uint32_t st, const vec_t<T>& g) {
+        const int s = (int)(st & 0xffffu), t = (int)(st >> 16);
+        vec_t<T> ps = P[s];
+        eps_t<T> es = Es[s];
+        T bs = ps.w;
+        vec_t<T> pt = P[t];
+        eps_t<T> et = Es[t];
+        ssa_pair_map(C, R, ps, es, bs, pt, et, g, k2, amp0);
+        ps.w = bs;
+        P[s] = ps;
+        Es[s] = es;
+        P[t] = pt;
+        Es[t] = et;
+    };
+    auto gauss = [&](uint32_t st, T w) {
+        const T3<T> G = pair_gauss<T>(C.seed, step, (uint32_t)rep, ID[st & 0xffffu], ID[st >> 16]);
+        vec_t<T> g;
+        g.x = G.x;
+        g.y = G.y;
+        g.z = G.z;
+        g.w = w;
+        return g;
+    };
+    // level starts o[l] for l = 0..nlev, read three levels ahead
+    auto lv_start = [&](int l) { return l <= nlev ? __ldg(lvo + l) : 0; };
+    int o0 = lv_start(0), o1 = lv_start(1), o2 = lv_start(2), o3 = lv_start(3);
+    // pass-0 records of levels 0 and 1
+    bool v0 = 0 < nlev && o0 + tid < o1, v1 = 1 < nlev && o1 + tid < o2;
+    uint32_t st0 = v0 ? __ldg(rst + o0 + tid) : 0u, st1 = v1 ? __ldg(rst + o1 + tid) : 0u;
+    T w0 = v0 ? __ldg(rw + o0 + tid) : T(0), w1 = v1 ? __ldg(rw + o1 + tid) : T(0);
+    vec_t<T> g0 = gauss(st0, w0);
+    for (int l = 0; l < nlev; ++l) {
+        // record of level l + 2
+        const bool v2 = l + 2 < nlev && o2 + tid < o3;
+        const uint32_t st2 = v2 ? __ldg(rst + o2 + tid) : 0u;
+        const T w2 = v2 ? __ldg(rw + o2 + tid) : T(0);
+        const int o4 = lv_start(l + 4);
+        // Gaussian of level l + 1, then the map of level l
+        const vec_t<T> g1 = gauss(st1, w1);
+        if (v0) apply(st0, g0);
+        for (int r = o0 + tid + blockDim.x; r < o1; r += blockDim.x) {
+            const uint32_t st = __ldg(rst + r);
+            apply(st, gauss(st, __ldg(rw + r)));
+        }
+        __syncthreads();
+        o0 = o1; o1 = o2; o2 = o3; o3 = o4;
+        v0 = v1; st0 = st1; g0 = g1;
+        v1 = v2; st1 = st2; w1 = w2;
+    }
+}
+
+// Domain d without a schedule: its colour classes in order on the state in
+// global memory, a thread per cell of the class (the colour order itself).
+template <class T>
+__device__ void ssa_exec_classes(const Ctx<T>& C, const SsaDomains& D, int d, int rep, T dt, T sqrt_dt) {
+    const RepInfo& R = C.reps[rep];
+    const T amp0 = T(2) * C.sigma * sqrt_dt;
+    const T k2 = T(2) * dt * C.inv_m;
+    const uint32_t step = (uint32_t)*C.step;
+    const size_t N = (size_t)C.N;
+    const int* off = D.off + (size_t)d * (NCOLOURS + 1);
+    for (int k = 0; k < NCOLOURS; ++k) {
+        const int k0 = off[k], k1 = off[k + 1];
+        if (k1 == k0) continue;
+        for (int u = k0 + threadIdx.x; u < k1; u += blockDim.x) {
+            const int c = D.cells[u];
+            for (int s = C.start[c]; s < C.start[c + 1]; ++s) {
+                const int nf = C.fwd_n[s];
+                if (nf == 0) continue;
+                vec_t<T> ps = C.pB[s];
+                eps_t<T> es = C.eB[s];
+                T bs = ps.w;
+                const uint32_t ids = C.idB[s];
+                for (int m = 0; m < nf; ++m) {
+                    const int t = C.fwd_j[(size_t)m * N + s];
+                    const T3<T> G = pair_gauss<T>(C.seed, step, (uint32_t)rep, ids, C.idB[t]);
+                    vec_t<T> g;
+                    g.x = G.x;
+                    g.y = G.y;
+                    g.z = G.z;
+                    g.w = C.fwd_w[(size_t)m * N + s];
+                    vec_t<T> pt = C.pB[t];
+                    eps_t<T> et = C.eB[t];
+                    ssa_pair_map(C, R, ps, es, bs, pt, et, g, k2, amp0);
+                    C.pB[t] = pt;
+                    C.eB[t] = et;
+                }
+                ps.w = bs;
+                C.pB[s] = ps;
+                C.eB[s] = es;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// One domain on the calling block: staged in shared memory when it fits in
+// scap slots, else deferred (regular form) or run on global memory (dense
+// form, defer == nullptr).
+template <class T>
+__device__ void ssa_exec_domain(const Ctx<T>& C, const SsaDomains& D, const SsaLevels<T>& V, int d, int scap,
+                                int* defer, int* ndefer, T dt, T sqrt_dt, unsigned char* smem) {
+    int sb, se;
+    ssa_domain_range(C, D, d, sb, se);
+    const int nb = se - sb;
+    if (nb == 0) return;
+    const int nlev = V.lv_n[d];
+    const int rep = C.rep_of_cell[D.cell0[d]];
+    if (nlev < 0) {   // no schedule, even with the dense capacities: the colour order itself
+        ssa_exec_classes(C, D, d, rep, dt, sqrt_dt);
+        return;
+    }
+    if (nb > scap) {
+        if (defer) {
+            if (threadIdx.x == 0) defer[atomicAdd(ndefer, 1)] = d;
+            return;
+        }
+        ssa_exec_levels(C, V, d, sb, rep, C.pB + sb, C.eB + sb, C.idB + sb, dt, sqrt_dt);
+        return;
+    }
+    vec_t<T>* P = reinterpret_cast<vec_t<T>*>(((size_t)smem + 31) & ~(size_t)31);
+    eps_t<T>* Es = reinterpret_cast<eps_t<T>*>(P + scap);
+    uint32_t* ID = reinterpret_cast<uint32_t*>(Es + scap);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        P[i] = C.pB[sb + i];
+        Es[i] = C.eB[sb + i];
+        ID[i] = C.idB[sb + i];
+    }
+    __syncthreads();
+    ssa_exec_levels(C, V, d, sb, rep, P, Es, ID, dt, sqrt_dt);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        C.pB[sb + i] = P[i];
+        C.eB[sb + i] = Es[i];
+    }
+}
+
+// Regular form (list == nullptr): block d takes domain d and defers it when
+// it has more than scap particles. Dense form: the blocks loop over `list`,
+// the deferred domains.
+template <class T>
+__global__ void __launch_bounds__(SSA_EXEC_THREADS_MAX) k_ssa_exec(Ctx<T> C, SsaDomains D, SsaLevels<T> V,
+                                                                    int scap, const int* __restrict__ list,
+                                                                    const int* __restrict__ nlist, int* defer,
+                                                                    int* ndefer, T dt, T sqrt_dt) {
+    extern __shared__ __align__(16) unsigned char exec_smem[];
+    if (!list) {
+        ssa_exec_domain(C, D, V, blockIdx.x, scap, defer, ndefer, dt, sqrt_dt, exec_smem);
+        return;
+    }
+    const int n = *nlist;
+    for (int u = blockIdx.x; u < n; u += gridDim.x) {
+        ssa_exec_domain(C, D, V, list[u], scap, nullptr, nullptr, dt, sqrt_dt, exec_smem);
+        __syncthreads();
+    }
+}
+
+}  // namespace dpde

@@ -151,7 +151,7 @@ def test_walled_ssa_forms_agree_bit_for_bit(precision):
     specs = [(1500, (7.0, 7.0, 10.3), 50.0, 1.0, (1, 1, 3)), (800, (5.5, 5.5, 9.1), 50.0, 1.0, (1, 1, 1))]
     q, p, e = make_state(specs, 64, precision == "mixed")
     outs = []
-    for mode in (0, 1):
+    for mode in (0, 1, 2):
         S = dpde.System(dpde.make_params(precision=precision),
                         [dpde.make_replica(n, box, cv, br, 1, -0.7) for n, box, cv, _, br in specs])
         S.set_tuning(ssa_mode=mode)
@@ -159,8 +159,9 @@ def test_walled_ssa_forms_agree_bit_for_bit(precision):
         S.step(6, 0.01, "HYBRID")
         outs.append(S.get_state())
         S.close()
-    for a, b in zip(*outs):
-        assert np.array_equal(a, b)
+    for out in outs[1:]:
+        for a, b in zip(outs[0], out):
+            assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -397,6 +398,10 @@ def test_ssa_launches_follow_colour_classes(box, bricks):
     S.set_tuning(ssa_mode=1)
     assert S.step_launches("HYBRID") - ser == 2
     assert S.step_launches("SSA") == ssa
+    # level form: two schedule and two execution launches, for bricks and whole replicas
+    S.set_tuning(ssa_mode=2)
+    assert S.step_launches("HYBRID") - ser == 4
+    assert S.step_launches("SSA") - (ser - 1) == 4
     S.close()
 
 
@@ -549,7 +554,8 @@ def test_ssa_modes_agree_bit_for_bit(precision, scheme):
     ref = _run_tuned(precision, {"ssa_mode": 0}, scheme=scheme)
     for t in ({"ssa_mode": 1}, {"ssa_mode": 1, "ssa_block": 32}, {"ssa_mode": 1, "ssa_block": 128},
               {"ssa_mode": 1, "ssa_group": 1}, {"ssa_mode": 1, "ssa_group": 3},
-              {"ssa_mode": 1, "ssa_group": 8, "ssa_block": 96}):
+              {"ssa_mode": 1, "ssa_group": 8, "ssa_block": 96},
+              {"ssa_mode": 2}, {"ssa_mode": 2, "ssa_block": 32}, {"ssa_mode": 2, "ssa_block": 128}):
         got = _run_tuned(precision, t, scheme=scheme)
         for a, b in zip(ref, got):
             assert np.array_equal(a, b), t
@@ -565,7 +571,7 @@ def test_ssa_modes_agree_on_thin_and_batched_boxes(scheme):
              (2000, (4.1, 9.0, 16.5), 80.0, 1.0, (1, 3, 1))]
     q, p, e = make_state(specs, 91, True)
     outs = []
-    for mode, group in ((0, 0), (1, 0), (1, 2), (1, 5)):
+    for mode, group in ((0, 0), (1, 0), (1, 2), (1, 5), (2, 0)):
         S = dpde.System(dpde.make_params(precision="mixed"),
                         [dpde.make_replica(n, box, cv, br) for n, box, cv, _, br in specs])
         S.set_tuning(ssa_mode=mode, ssa_group=group)
@@ -577,6 +583,45 @@ def test_ssa_modes_agree_on_thin_and_batched_boxes(scheme):
     for out in outs[1:]:
         for a, b in zip(outs[0], out):
             assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["dense_brick", "global_state", "no_schedule"])
+def test_ssa_level_form_fallbacks_agree_bit_for_bit(precision, case):
+    """The level form's paths beyond its regular shared-memory capacities give
+    the colour order's bits: a brick holding more particles than the regular
+    execution stages (deferred to the launch with larger capacities); one
+    domain too large for any staging (levels run on the state in global
+    memory); one domain with more forward entries than a schedule holds (run
+    class by class along the colour order)."""
+    from paper_1507_06643_gb300 import dpde
+    rng = np.random.default_rng(41)
+    if case == "dense_brick":
+        n0, L, bricks = 4000, cube(4000), (2, 2, 2)
+        q, p, e = make_state([(n0, (L,) * 3, 50.0, 1.0, bricks)], 42, precision == "mixed")
+        extra = 0.25 * L + rng.uniform(-2.0, 2.0, (300, 3))   # inside brick (0, 0, 0), density ~8 there
+        q = np.vstack([q, extra])
+        p = np.vstack([p, rng.standard_normal((300, 3))])
+        e = np.concatenate([e, 50.0 * (1 + 0.05 * rng.uniform(-1, 1, 300))])
+        if precision == "mixed":
+            q = q.astype(np.float32).astype(np.float64)
+            p = p.astype(np.float32).astype(np.float64)
+        n = n0 + 300
+    else:
+        n = 8000 if case == "global_state" else 15000
+        L, bricks = cube(n), (1, 1, 1)
+        q, p, e = make_state([(n, (L,) * 3, 50.0, 1.0, bricks)], 43, precision == "mixed")
+    outs = []
+    for mode in (0, 2):
+        S = dpde.System(dpde.make_params(precision=precision), [dpde.make_replica(n, (L,) * 3, 50.0, bricks)])
+        S.set_tuning(ssa_mode=mode)
+        S.set_state(q, p, e)
+        S.step(3, 0.01, "HYBRID")
+        assert S.sync() == dpde.DPDE_OK
+        outs.append(S.get_state())
+        S.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("edge", [2, 4, 5, 8])
@@ -598,7 +643,7 @@ def test_autotune_keeps_the_state():
     step0 = dpde.dpde_get_step(S.h)
     t = S.autotune("HYBRID", 0.01, 2)
     assert t["tile_edge"] in (4, 5, 6, 7, 8) and t["block"] in (128, 256, 512)
-    assert t["ssa_block"] in (32, 64, 128) and t["ssa_mode"] in (0, 1) and t["ms_per_step"] > 0
+    assert t["ssa_block"] in (32, 64, 128) and t["ssa_mode"] in (0, 1, 2) and t["ms_per_step"] > 0
     assert 1 <= t["ssa_group"] <= 8
     assert S.tuning()["tile_edge"] == t["tile_edge"]
     after = S.get_state()
@@ -624,7 +669,7 @@ def test_bad_tuning_rejected():
     from paper_1507_06643_gb300 import dpde
     S = dpde.System(dpde.make_params(precision="mixed"), [dpde.make_replica(300, (cube(300),) * 3, 50.0)])
     for kw in ({"tile_edge": 1}, {"tile_edge": 9}, {"block": 48}, {"block": 2048}, {"ssa_block": 256},
-               {"ssa_block": 48}, {"ssa_mode": 2}, {"ssa_mode": -1}, {"ssa_group": 9}, {"ssa_group": -1}):
+               {"ssa_block": 48}, {"ssa_mode": 3}, {"ssa_mode": -1}, {"ssa_group": 9}, {"ssa_group": -1}):
         with pytest.raises(dpde.DPDEError):
             S.set_tuning(**kw)
     S.close()
@@ -649,6 +694,33 @@ def test_negative_and_nonfinite_state_reported():
     assert ei.value.code == dpde.DPDE_ERR_NONFINITE
     S.set_state(q, p, e)     # a clean state clears the condition
     S.step(2, 0.01, "SER")
+    assert S.sync() == dpde.DPDE_OK
+    S.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("scheme", ["SER", "HYBRID", "SSA"])
+def test_neighbour_list_overflow_reported(precision, scheme):
+    """A host-built dense cluster -- 150 particles within 0.25 of one point in
+    a fluid at density 3 -- gives each of them ~150 neighbours, beyond the list
+    capacity (3 x the mean count + 32, ~70 at density 3). The step completes
+    with the lists truncated (no write past them) and dpde_sync reports
+    DPDE_ERR_CAPACITY; after a clean state the condition is gone."""
+    from paper_1507_06643_gb300 import dpde
+    n = 1500
+    L = cube(n)
+    specs = [(n, (L,) * 3, 100.0, 1.0, (2, 2, 2))]
+    q, p, e = make_state(specs, 31, precision == "mixed")
+    rng = np.random.default_rng(32)
+    q2 = q.copy()
+    q2[:150] = 0.5 * L + rng.uniform(-0.25, 0.25, (150, 3))
+    S = dpde.System(dpde.make_params(precision=precision), [dpde.make_replica(n, (L,) * 3, 100.0, (2, 2, 2))])
+    S.set_state(q2, p, e)
+    S.step(1, 0.01, scheme)
+    assert S.sync() == dpde.DPDE_ERR_CAPACITY
+    assert "capacity" in dpde.lib().dpde_last_error(S.h).decode()
+    S.set_state(q, p, e)
+    S.step(2, 0.01, scheme)
     assert S.sync() == dpde.DPDE_OK
     S.close()
 
@@ -678,6 +750,7 @@ def test_full_size_large_n4m_one_step(precision, scheme):
             keep[lst] = False
         assert keep.mean() > 0.99, keep.mean()
     dq = q_diff(qg, ref.q, [spec.box], ref.offsets)
-    e = {"q": float(np.max(np.abs(dq[keep])) / np.max(np.abs(ref.q))),
+    moved = q_diff(ref.q, state[0], [spec.box], ref.offsets)   # the oracle's displacement from the start
+    e = {"q": float(np.max(np.abs(dq[keep])) / np.max(np.abs(moved))),
          "p": rel_err(pg[keep], ref.p[keep]), "eps": rel_err(eg[keep], ref.eps[keep])}
     assert max(e.values()) < TOL[precision], (e, len(flips))
