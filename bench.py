@@ -305,9 +305,11 @@ def run_ours(args):
         "gpu_launches": None,
         "roofline": roofline,
         "phase_ms": phase_avg,
-        "energy": {"rel_drift_over_timed_steps": drift, "steps": args.steps + args.warmup,
-                   "after_steps": args.warmup,
-                   "status": status},
+        "energy_transient": {"rel_change_over_timed_steps": drift, "after_steps": 2 * args.warmup,
+                             "status": status,
+                             "note": "from an unrelaxed uniform-random start: the overlap energy relaxing, "
+                                     "not the scheme's drift; the stated drift is energy_drift (relaxed 108k "
+                                     "fluid)"},
     }
     nlaunch = S.step_launches(args.scheme)
     out["gpu_launches"] = nlaunch * args.steps
@@ -318,11 +320,17 @@ def run_ours(args):
         out["speedup_mixed_over_fp64"] = value / (f64["value"] * world)
     if args.drift_steps > 0:
         out["energy_drift"] = drift_run(args, stream)
+    if args.shock_steps > 0:
+        out["shock"] = shock_run(args, stream)
+    if args.batched_steps > 0:
+        out["batched"] = batched_run(args, stream)
     if rank == 0:
         out["clocks"] = clk.summary()
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"], base = cpu_baseline(w, args.scheme, args.cpu_seconds)
             out["parity"] = parity_report(w, base, args.scheme)
+            if args.batched_steps > 0:
+                out["cpu_baseline_batched"] = cpu_batched_baseline()
         print(json.dumps(out))
     if world > 1:
         tdist.destroy_process_group()
@@ -349,51 +357,155 @@ def fp64_run(args, spec_reps, w, q, p, e, stream):
             "warmup": 3, "ms_per_step": ms / args.fp64_steps, "dtype": "f64"}
 
 
+def _energy_series(S, steps, dt, scheme, every):
+    """E sampled every `every` steps over `steps` steps (E^0 first), with the
+    mean kinetic and internal temperatures over the samples."""
+    o = S.observables(check=True)[0]
+    Es, tk, ti = [o["E"]], [], []
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        S.step(k, dt, scheme)
+        done += k
+        o = S.observables(check=True)[0]
+        Es.append(o["E"])
+        tk.append(o["Tkin"])
+        ti.append(o["Tint"])
+    return np.asarray(Es), float(np.mean(tk)), float(np.mean(ti))
+
+
 def drift_run(args, stream):
-    """Total-energy drift on the N=108,000 equilibrium fluid: max over samples
-    every `every` steps of |E^n - E^0| / |E^0| after an equilibration, with
-    the mean kinetic and internal temperatures over the samples, in mixed
-    and FP64 modes (same seed and initial state)."""
+    """Total-energy drift on the N=108,000 equilibrium fluid (Sec. IV.B).
+
+    The fluid is relaxed first (Hybrid at dt = 0.01); from that one state
+    both precisions then run at the drift timestep with the same noise: the
+    mixed mode for --drift-steps, FP64 for --drift-steps-fp64. Reported:
+    max_n |E^n - E^0| / |E^0| and the fitted drift rate of each run, and the
+    precision-induced part max |(E_m^n - E_m^0) - (E_f^n - E_f^0)| / |E^0|
+    over the steps both ran. At dt = 0.0035 the scheme's own drift (rate
+    ~ dt^4, Sec. IV.B) over 1e5 steps is expected below 1e-6."""
     from paper_1507_06643_gb300 import dpde, inputs
+    dt = args.drift_dt
+    steps = {"mixed": args.drift_steps, "fp64": args.drift_steps_fp64 or args.drift_steps}
     out = {"workload": "equilibrium_n108000", "scheme": args.scheme, "equilibration_steps": args.drift_equil,
-           "steps": args.drift_steps}
-    every = max(1, min(1000, args.drift_steps // 10))
+           "equilibration_dt": 0.01, "dt": dt, "steps": steps}
+    w = inputs.equilibrium_n108000("mixed")
+    reps = [dpde.make_replica(x.n, x.box, x.cv, x.bricks, x.walls, x.wall_u) for x in w.replicas]
+    q, p, e = inputs.workload_state(w)
+    R = dpde.System(dpde.make_params(w.mass, w.r_cut, w.a, w.sigma, w.seed, "mixed"), reps, stream=stream.cuda_stream)
+    R.set_state(q, p, e)
+    R.step(args.drift_equil, 0.01, args.scheme)
+    q, p, e = R.get_state()
+    R.close()
+    every = max(1, min(1000, min(steps.values()) // 20))
+    series = {}
     for prec in ("mixed", "fp64"):
-        w = inputs.equilibrium_n108000(prec)
-        reps = [dpde.make_replica(x.n, x.box, x.cv, x.bricks, x.walls, x.wall_u) for x in w.replicas]
-        S = dpde.System(dpde.make_params(w.mass, w.r_cut, w.a, w.sigma, w.seed, prec), reps,
+        S = dpde.System(dpde.make_params(w.mass, w.r_cut, w.a, w.sigma, w.seed + 1, prec), reps,
                         stream=stream.cuda_stream)
-        q, p, e = inputs.workload_state(w)
         S.set_state(q, p, e)
-        S.step(args.drift_equil, w.dt, args.scheme)
-        o0 = S.observables(check=True)[0]
-        E0, dev, tk, ti, Es = o0["E"], 0.0, [], [], [o0["E"]]
-        done = 0
         t = time.perf_counter()
-        while done < args.drift_steps:
-            k = min(every, args.drift_steps - done)
-            S.step(k, w.dt, args.scheme)
-            done += k
-            o = S.observables(check=True)[0]
-            dev = max(dev, abs(o["E"] - E0) / abs(E0))
-            Es.append(o["E"])
-            tk.append(o["Tkin"])
-            ti.append(o["Tint"])
+        Es, tk, ti = _energy_series(S, steps[prec], dt, args.scheme, every)
         el = time.perf_counter() - t
         S.close()
-        out[prec] = {"max_rel_drift": dev, "final_rel_drift": abs(o["E"] - E0) / abs(E0),
-                     "mean_Tkin": float(np.mean(tk)), "mean_Tint": float(np.mean(ti)),
-                     "wall_s": el, "E": Es}
-    # precision-induced part: both runs share the initial state and the noise
-    # drift rate: least-squares slope of (E^n - E^0)/|E^0| against time
-    for prec in ("mixed", "fp64"):
-        Es = np.asarray(out[prec]["E"])
-        tt = np.arange(len(Es)) * every * w.dt
-        out[prec]["alpha_per_unit_time"] = float(np.polyfit(tt, (Es - Es[0]) / abs(Es[0]), 1)[0]) if len(Es) > 2 else None
-    em, ef = np.asarray(out["mixed"].pop("E")), np.asarray(out["fp64"].pop("E"))
+        rel = (Es - Es[0]) / abs(Es[0])
+        tt = np.arange(len(Es)) * every * dt
+        out[prec] = {"max_rel_drift": float(np.max(np.abs(rel))), "final_rel_drift": float(abs(rel[-1])),
+                     "alpha_per_unit_time": float(np.polyfit(tt, rel, 1)[0]) if len(Es) > 2 else None,
+                     "mean_Tkin": tk, "mean_Tint": ti, "wall_s": el, "steps": steps[prec]}
+        series[prec] = Es
+    n = min(len(series["mixed"]), len(series["fp64"]))
+    em, ef = series["mixed"][:n], series["fp64"][:n]
     out["max_rel_drift_mixed_minus_fp64"] = float(np.max(np.abs((em - em[0]) - (ef - ef[0]))) / abs(ef[0]))
+    out["common_steps"] = (n - 1) * every
     out["sample_every"] = every
+    out["bar"] = {"rel_drift": 1e-6, "steps": 100000,
+                  "mixed_meets_bar": bool(out["mixed"]["max_rel_drift"] < 1e-6 and steps["mixed"] >= 100000)}
     return out
+
+
+def shock_run(args, stream):
+    """The shock workload (BASELINE config 4: box 40 x 40 x 800 at density 3,
+    halves at +-2 along z, C_v = 100, dt = 0.005, mixed precision, Hybrid):
+    throughput, total-energy drift over --shock-steps steps, and the mean
+    internal energy in 800 slabs along z at the start, halfway and at the
+    end (the analogue of the eps profiles of Sec. V)."""
+    import torch
+    from paper_1507_06643_gb300 import dpde, inputs
+    w = inputs.shock_40x40x800("mixed")
+    spec = w.replicas[0]
+    reps = [dpde.make_replica(spec.n, spec.box, spec.cv, spec.bricks, spec.walls, spec.wall_u)]
+    S = dpde.System(dpde.make_params(w.mass, w.r_cut, w.a, w.sigma, w.seed, "mixed"), reps, stream=stream.cuda_stream)
+    q, p, e = inputs.workload_state(w)
+    S.set_state(q, p, e)
+    S.step(3, w.dt, "HYBRID")
+    S.sync()
+    nsl = 800
+    Lz = spec.box[2]
+
+    def profile():
+        qq, _, ee = S.get_state()
+        idx = np.minimum((qq[:, 2] / Lz * nsl).astype(np.int64), nsl - 1)
+        cnt = np.bincount(idx, minlength=nsl)
+        return np.bincount(idx, weights=ee, minlength=nsl) / np.maximum(cnt, 1)
+
+    o0 = S.observables(check=False)[0]
+    prof = {"t0": profile()}
+    half = args.shock_steps // 2
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    S.step(half, w.dt, "HYBRID")
+    t1.record(stream)
+    t1.synchronize()
+    ms = t0.elapsed_time(t1)
+    prof["half"] = profile()
+    S.step(args.shock_steps - half, w.dt, "HYBRID")
+    status = S.sync()
+    o1 = S.observables(check=False)[0]
+    prof["end"] = profile()
+    S.close()
+    return {"workload": w.name, "n": spec.n, "dt": w.dt, "steps": args.shock_steps, "scheme": "HYBRID",
+            "precision": "mixed", "value": spec.n * half / (ms / 1e3), "unit": UNIT, "timed_steps": half,
+            "ms_per_step": ms / half, "rel_drift": abs(o1["E"] - o0["E"]) / abs(o0["E"]), "status": status,
+            "neg_eps": o1["neg_eps"], "eps_profile": {"slabs": nsl, "slab_width": Lz / nsl,
+                                                      "times": [0.0, half * w.dt, args.shock_steps * w.dt],
+                                                      **{k: [round(float(x), 3) for x in v] for k, v in prof.items()}}}
+
+
+def batched_run(args, stream):
+    """The batched workload (BASELINE config 5: 256 systems of 2,000-64,000
+    particles, kT in [0.5, 2], C_v in {10, 50, 100}, mixed, Hybrid): all
+    replicas advance in the same launches; throughput and the largest
+    relative energy change of a replica over the timed steps."""
+    import torch
+    from paper_1507_06643_gb300 import dpde, inputs
+    w = inputs.batched_256("mixed")
+    reps = [dpde.make_replica(x.n, x.box, x.cv, x.bricks, x.walls, x.wall_u) for x in w.replicas]
+    S = dpde.System(dpde.make_params(w.mass, w.r_cut, w.a, w.sigma, w.seed, "mixed"), reps, stream=stream.cuda_stream)
+    q, p, e = inputs.workload_state(w)
+    S.set_state(q, p, e)
+    S.step(200, w.dt, "HYBRID")
+    S.sync()
+    tuning = S.autotune("HYBRID", w.dt, 5)
+    o0 = S.observables(check=False)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    S.step(args.batched_steps, w.dt, "HYBRID")
+    t1.record(stream)
+    t1.synchronize()
+    ms = t0.elapsed_time(t1)
+    status = S.sync()
+    o1 = S.observables(check=False)
+    launches = S.step_launches("HYBRID")
+    S.close()
+    drift = max(abs(b["E"] - a["E"]) / abs(a["E"]) for a, b in zip(o0, o1))
+    return {"workload": w.name, "replicas": len(reps), "n": w.n_total, "dt": w.dt, "steps": args.batched_steps,
+            "value": w.n_total * args.batched_steps / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms / args.batched_steps, "launches_per_step": launches,
+            "max_replica_rel_drift": drift, "after_steps": 200, "status": status,
+            "neg_eps_replicas": int(sum(1 for o in o1 if o["neg_eps"] > 0)),
+            "tuning": {k: tuning[k] for k in ("tile_edge", "block", "ssa_block", "ssa_mode", "ssa_group")}}
 
 
 def oracle_sample(w, n_target: int):
@@ -415,6 +527,67 @@ def oracle_sample(w, n_target: int):
     return sub
 
 
+def host_cpu():
+    """Core count and CPU model of the host the oracle runs on."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "model": model or "unknown"}
+
+
+def _oracle_replica_rate(job):
+    """One replica advanced by the oracle in a worker process: returns
+    (particles, steps, seconds)."""
+    from oracle import oracle as O
+    n, box, cv, kT, bricks, seed, steps, dt = job
+    from paper_1507_06643_gb300 import inputs
+    spec = inputs.ReplicaSpec(n, box, cv, kT, bricks)
+    q, p, e = inputs.replica_state(spec, 1.0, np.random.default_rng(seed))
+    S = O.System([O.make_replica(n, box, cv, bricks)], O.make_params(seed=seed), q, p, e)
+    t = time.perf_counter()
+    S.run(steps, dt, "HYBRID")
+    return n, steps, time.perf_counter() - t
+
+
+def cpu_batched_baseline(nrep_per_core: int = 3, steps: int = 3):
+    """The oracle on the batched workload across all host cores: replicas of
+    batched_256 (independent systems) spread over a process pool (spawn),
+    one replica per task. Aggregate particle-steps/s = sum n_r steps /
+    wall time of the pool."""
+    import multiprocessing as mp
+    from paper_1507_06643_gb300 import inputs
+    cores = os.cpu_count() or 1
+    w = inputs.batched_256("fp64")
+    jobs = [(r.n, r.box, r.cv, r.kT, r.bricks, 2000 + k, steps, w.dt)
+            for k, r in enumerate(w.replicas[: nrep_per_core * cores])]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_replica_rate, jobs[:cores])          # warm the workers (imports, build)
+        t = time.perf_counter()
+        res = pool.map(_oracle_replica_rate, jobs)
+        el = time.perf_counter() - t
+    n_ps = sum(n * k for n, k, _ in res)
+    return {"value": n_ps / el, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": host_cpu(),
+            "sample": f"{len(jobs)} replicas of batched_256 ({sum(n for n, _, _ in res)} particles), {steps} "
+                      f"Hybrid steps each, FP64 oracle, one replica per task on a {cores}-process pool, "
+                      f"{el:.1f} s"}
+
+
 def cpu_baseline(w, scheme: str, seconds: float, steps: int | None = None):
     from oracle import oracle as O
     from paper_1507_06643_gb300 import inputs
@@ -429,7 +602,7 @@ def cpu_baseline(w, scheme: str, seconds: float, steps: int | None = None):
     t = time.perf_counter()
     S.run(nsteps, sub.dt, scheme)
     el = time.perf_counter() - t
-    out = {"value": spec.n * nsteps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    out = {"value": spec.n * nsteps / el, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": host_cpu(),
            "sample": f"{nsteps} step(s) of a {spec.n}-particle cubic sub-box of {w.name} "
                      f"(same density and parameters, FP64, {scheme}, bricks {spec.bricks}), "
                      f"{el:.1f} s"}
@@ -508,7 +681,7 @@ def run_reference(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": w.name, "scheme": args.scheme,
                                            "precision": "fp64", "sample_n": spec.n},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": host_cpu(),
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -534,9 +707,16 @@ def main():
     ap.add_argument("--ssa-group", type=int, default=None, help="force the Hybrid domains per warp (1..8)")
     ap.add_argument("--fp64-steps", type=int, default=20,
                     help="steps of the FP64 GPU run of the same workload (0: skip)")
-    ap.add_argument("--drift-steps", type=int, default=10000,
-                    help="measured steps of the energy-drift run on the 108k fluid (0: skip)")
+    ap.add_argument("--drift-steps", type=int, default=100000,
+                    help="steps of the mixed-precision energy-drift run on the 108k fluid (0: skip)")
+    ap.add_argument("--drift-steps-fp64", type=int, default=20000,
+                    help="steps of the FP64 run of the drift study (0: as many as the mixed run)")
+    ap.add_argument("--drift-dt", type=float, default=0.0035)
     ap.add_argument("--drift-equil", type=int, default=2000)
+    ap.add_argument("--shock-steps", type=int, default=20000,
+                    help="steps of the shock leg (40 x 40 x 800 box; 0: skip)")
+    ap.add_argument("--batched-steps", type=int, default=1000,
+                    help="timed steps of the batched leg (256 replicas; 0: skip)")
     ap.add_argument("--drift-only", action="store_true",
                     help="run only the energy-drift study and print its JSON")
     ap.add_argument("--bricks", default="",

@@ -39,7 +39,8 @@ namespace dpde {
 constexpr int SSA_MAXLEV = 1023;         // levels of one domain kept by the schedule
 constexpr int SSA_LV_STRIDE = SSA_MAXLEV + 2;
 constexpr int SCHED_THREADS = 128;
-constexpr int SSA_LOAD_BATCH = 8;       // global loads a thread keeps in flight
+constexpr int SSA_LOAD_BATCH = 8;       // entries of a row taken together by the level walk
+constexpr int SSA_ROW_BATCH = 4;        // entries per particle, two particles, loaded together
 constexpr int SSA_EXEC_THREADS_MAX = 128;
 constexpr int SSA_LOCAL_MAX = 65535;      // particles (and entries) of one domain: 16-bit local indices
 
@@ -68,9 +69,10 @@ struct SsaLevels {
 };
 
 // shared bytes of k_ssa_sched for scap particles and ecap entries:
-// cnt[SSA_MAXLEV + 2] | rowoff[scap + 1] | L[scap] | ent[ecap] (16-bit)
+// cnt (16-bit counters of levels 0..SSA_MAXLEV + 1, two to a word) |
+// rowoff[scap + 1] | L[scap] | ent[ecap] (16-bit)
 __host__ __device__ constexpr size_t ssa_sched_smem(int scap, int ecap) {
-    return (size_t)SSA_LV_STRIDE * sizeof(int) + (((size_t)(2 * scap + 1 + ecap) * 2 + 15) / 16) * 16;
+    return (size_t)(SSA_LV_STRIDE / 2 + 1) * sizeof(int) + (((size_t)(2 * scap + 1 + ecap) * 2 + 15) / 16) * 16;
 }
 // shared bytes of k_ssa_exec for scap staged particles: p | eps | id, after
 // up to 31 bytes that align p to 32 bytes
@@ -105,6 +107,43 @@ __device__ __forceinline__ int block_scan_runs(int n, unsigned short* out, int* 
     return total;
 }
 
+// 16-bit level counters, two to a 32-bit word (a domain has at most
+// SSA_LOCAL_MAX entries, so no count or offset reaches the upper half)
+__device__ __forceinline__ int cnt_add(int* cnt, int l) {
+    const int sh = (l & 1) << 4;
+    return (atomicAdd(cnt + (l >> 1), 1 << sh) >> sh) & 0xffff;
+}
+__device__ __forceinline__ int cnt_get(const int* cnt, int l) { return (cnt[l >> 1] >> ((l & 1) << 4)) & 0xffff; }
+
+// The rows of the domain's particles, two particles per thread at a time
+// (i and i + blockDim), the entries of both loaded together in chunks of
+// SSA_ROW_BATCH: f(i, e, m, k) is called for the k-th value of entry m of
+// particle i, whose row starts at rowoff[i] (e = rowoff[i] + m), with the
+// values loaded by load(i, m).
+template <class Load, class Use>
+__device__ __forceinline__ void ssa_rows_batched(int nb, const unsigned short* rowoff, Load&& load, Use&& use) {
+    const int bd = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < nb; i0 += 2 * bd) {
+        const int i1 = i0 + bd;
+        const int a0 = rowoff[i0], na = rowoff[i0 + 1] - a0;
+        const int b0 = i1 < nb ? rowoff[i1] : 0, nbv = i1 < nb ? rowoff[i1 + 1] - b0 : 0;
+        const int nmax = max(na, nbv);
+        for (int m0 = 0; m0 < nmax; m0 += SSA_ROW_BATCH) {
+            decltype(load(0, 0)) va[SSA_ROW_BATCH], vb[SSA_ROW_BATCH];
+#pragma unroll
+            for (int u = 0; u < SSA_ROW_BATCH; ++u) {
+                if (m0 + u < na) va[u] = load(i0, m0 + u);
+                if (m0 + u < nbv) vb[u] = load(i1, m0 + u);
+            }
+#pragma unroll
+            for (int u = 0; u < SSA_ROW_BATCH; ++u) {
+                if (m0 + u < na) use(i0, a0 + m0 + u, va[u]);
+                if (m0 + u < nbv) use(i1, b0 + m0 + u, vb[u]);
+            }
+        }
+    }
+}
+
 // One domain's schedule on the calling block. Returns false (nothing written)
 // when the domain exceeds scap particles, ecap entries or SSA_MAXLEV levels.
 template <class T>
@@ -118,82 +157,91 @@ __device__ bool ssa_sched_domain(const Ctx<T>& C, const SsaDomains& D, const Ssa
     const int tid = threadIdx.x;
     if (nb > scap || nb > SSA_LOCAL_MAX) return false;
     int* cnt = reinterpret_cast<int*>(smem);
-    unsigned short* rowoff = reinterpret_cast<unsigned short*>(cnt + SSA_LV_STRIDE);
+    unsigned short* rowoff = reinterpret_cast<unsigned short*>(cnt + SSA_LV_STRIDE / 2 + 1);
     unsigned short* L = rowoff + scap + 1;
     unsigned short* ent = L + scap;    // partner (local slot) of each entry, then its level
     if (tid == 0) {
         s_flag = 0;
         s_nlev = 0;
     }
-    for (int l = tid; l < SSA_LV_STRIDE; l += blockDim.x) cnt[l] = 0;
+    for (int l = tid; l <= SSA_LV_STRIDE / 2; l += blockDim.x) cnt[l] = 0;
     __syncthreads();
     // 1. row offsets of the domain's forward entries (16-bit: checked below)
     const int* fwd_n = C.fwd_n + sb;
     const int E = block_scan_runs(nb, rowoff, sh, [&](int i) { return fwd_n[i]; });
     if (E > ecap || E > SSA_LOCAL_MAX) return false;   // uniform over the block
     if (tid == 0) rowoff[nb] = (unsigned short)E;
+    for (int i = tid; i < nb; i += blockDim.x) L[i] = 0;
     __syncthreads();   // the rows' offsets were written by other threads
     const size_t N = (size_t)C.N;
-    // 2. partner slots, local: a thread per particle, its row's loads issued
-    //    together (entry m of particle s is at [m N + s])
-    for (int i = tid; i < nb; i += blockDim.x) {
-        L[i] = 0;
-        const int e0 = rowoff[i], nf = fwd_n[i];
-        const int* src = C.fwd_j + sb + i;
-        for (int m0 = 0; m0 < nf; m0 += SSA_LOAD_BATCH) {
-            int t[SSA_LOAD_BATCH];
-#pragma unroll
-            for (int u = 0; u < SSA_LOAD_BATCH; ++u)
-                t[u] = m0 + u < nf ? __ldg(src + (size_t)(m0 + u) * N) - sb : 0;
-#pragma unroll
-            for (int u = 0; u < SSA_LOAD_BATCH; ++u)
-                if (m0 + u < nf) {
-                    if ((unsigned)t[u] >= (unsigned)nb) s_flag = 1;   // never by construction
-                    ent[e0 + m0 + u] = (unsigned short)min(max(t[u], 0), nb - 1);
-                }
-        }
-    }
+    const int* fj = C.fwd_j + sb;   // entry m of local particle i at fj[m N + i]
+    const T* fw = C.fwd_w + sb;
+    // 2. partner slots, local
+    ssa_rows_batched(
+        nb, rowoff, [&](int i, int m) { return __ldg(fj + (size_t)m * N + i) - sb; },
+        [&](int, int e, int t) {
+            if ((unsigned)t >= (unsigned)nb) s_flag = 1;   // never by construction
+            ent[e] = (unsigned short)min(max(t, 0), nb - 1);
+        });
     __syncthreads();
     if (s_flag) {
         if (tid == 0) flag(C.status, ST_DOMAIN);
         return false;
     }
-    // 3. levels, class by class (a thread per cell of the class). The
-    //    partners of one row are distinct particles, so a row is taken in
-    //    chunks: partners and their levels loaded together, the chain of
-    //    maxima run in registers, the new levels stored together.
+    // 3. levels, class by class. Eight lanes take one cell of the class (the
+    //    cells of a class share no particle) and walk its rows -- the cell's
+    //    particles in slot order -- a chunk of up to eight entries at a time:
+    //    the partners of a row are distinct particles, so their levels are
+    //    loaded at once, and within the chunk the levels follow from a
+    //    prefix maximum across the lanes,
+    //      lev_j = j + 1 + max(L_s, max_{k <= j} (L[t_k] - k)),
+    //    which is the recurrence lev_j = 1 + max(lev_{j-1}, L[t_j]) unrolled.
     const int* off = D.off + (size_t)d * (NCOLOURS + 1);
+    const int lane = tid & 31, sub = lane & 7, gbase = lane & ~7;
+    const int group = tid >> 3, ngroups = blockDim.x >> 3;
     int mylev = 0;
     for (int k = 0; k < NCOLOURS; ++k) {
-        const int k0 = off[k], k1 = off[k + 1];
+        const int k0 = __ldg(off + k), k1 = __ldg(off + k + 1);
         if (k1 == k0) continue;   // uniform over the block
-        for (int u = k0 + tid; u < k1; u += blockDim.x) {
-            const int c = D.cells[u];
-            const int s0 = C.start[c] - sb, s1 = C.start[c + 1] - sb;
-            for (int i = s0; i < s1; ++i) {
-                int Ls = L[i];
-                const int e1 = rowoff[i + 1];
-                for (int eb = rowoff[i]; eb < e1; eb += SSA_LOAD_BATCH) {
-                    int t[SSA_LOAD_BATCH], lt[SSA_LOAD_BATCH];
+        for (int u0 = k0; u0 < k1; u0 += ngroups) {   // uniform over the block
+            const int u = u0 + group;
+            int s0 = 0, nrow = 0;
+            if (u < k1) {
+                const int c = __ldg(D.cells + u);
+                s0 = C.start[c] - sb;
+                nrow = C.start[c + 1] - sb - s0;
+            }
+            const int wrows = __reduce_max_sync(0xffffffffu, nrow);
+            for (int r = 0; r < wrows; ++r) {
+                const bool ract = r < nrow;
+                const int i = s0 + r;
+                int Ls = ract ? L[i] : 0;
+                const int e0 = ract ? rowoff[i] : 0, n = ract ? rowoff[i + 1] - e0 : 0;
+                const int wchunks = __reduce_max_sync(0xffffffffu, (n + 7) >> 3);
+                for (int ch = 0; ch < wchunks; ++ch) {
+                    const int j = (ch << 3) + sub;   // entry of the row
+                    const bool ea = j < n;
+                    const int t = ea ? ent[e0 + j] : 0;
+                    int a = ea ? (int)L[t] - sub : -65536;
 #pragma unroll
-                    for (int v = 0; v < SSA_LOAD_BATCH; ++v) t[v] = eb + v < e1 ? ent[eb + v] : 0;
-#pragma unroll
-                    for (int v = 0; v < SSA_LOAD_BATCH; ++v) lt[v] = L[t[v]];
-#pragma unroll
-                    for (int v = 0; v < SSA_LOAD_BATCH; ++v)
-                        if (eb + v < e1) {
-                            Ls = min(max(Ls, lt[v]) + 1, 65535);
-                            lt[v] = Ls;
-                        }
-#pragma unroll
-                    for (int v = 0; v < SSA_LOAD_BATCH; ++v)
-                        if (eb + v < e1) {
-                            L[t[v]] = (unsigned short)lt[v];
-                            ent[eb + v] = (unsigned short)lt[v];
-                        }
+                    for (int o = 1; o < 8; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, a, o, 8);
+                        if (sub >= o) a = max(a, y);
+                    }
+                    const int lv = min(max(Ls, a) + sub + 1, 65535);
+                    if (ea) {
+                        L[t] = (unsigned short)lv;
+                        ent[e0 + j] = (unsigned short)lv;
+                    }
+                    const int last = min(n - (ch << 3), 8) - 1;   // last entry of this chunk
+                    const int lvl = __shfl_sync(0xffffffffu, lv, gbase + max(last, 0));
+                    if (last >= 0) Ls = lvl;
                 }
-                L[i] = (unsigned short)Ls;
-                mylev = max(mylev, Ls);
+                if (ract) {
+                    if (sub == 0) L[i] = (unsigned short)Ls;
+                    mylev = max(mylev, Ls);
+                }
+                __syncwarp();   // the row's level writes, before the next row reads them
             }
         }
         __syncthreads();
@@ -203,53 +251,52 @@ __device__ bool ssa_sched_domain(const Ctx<T>& C, const SsaDomains& D, const Ssa
     const int nlev = s_nlev;
     if (nlev > SSA_MAXLEV) return false;
     // 4. records sorted by level: counts, offsets, scatter
-    for (int e = tid; e < E; e += blockDim.x) atomicAdd(&cnt[ent[e]], 1);
+    for (int e = tid; e < E; e += blockDim.x) cnt_add(cnt, ent[e]);
     __syncthreads();
+    int* lvo = V.lv_off + (size_t)d * SSA_LV_STRIDE;
     if (tid < 32) {
-        // exclusive scan of cnt[1..nlev] by one warp, into cnt[1..nlev + 1]
+        // exclusive scan of the counts of levels 1..nlev: lvo[l - 1] = start
+        // of level l, lvo[nlev] = E; the counters become the cursors
         int carry = 0;
         for (int l0 = 1; l0 <= nlev + 1; l0 += 32) {
             const int l = l0 + tid;
-            const int v = l <= nlev ? cnt[l] : 0;
+            const int v = l <= nlev ? cnt_get(cnt, l) : 0;
             int x = v;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, x, o);
                 if (tid >= o) x += y;
             }
-            if (l <= nlev + 1) cnt[l] = carry + x - v;
+            if (l <= nlev + 1) lvo[l - 1] = carry + x - v;
             carry += __shfl_sync(0xffffffffu, x, 31);
         }
     }
     __syncthreads();
-    int* lvo = V.lv_off + (size_t)d * SSA_LV_STRIDE;
-    for (int l = tid; l <= nlev; l += blockDim.x) lvo[l] = cnt[l + 1];
+    for (int l = tid; l <= SSA_LV_STRIDE / 2; l += blockDim.x) {
+        // cursor pair (2l, 2l + 1) = level starts (lvo[2l - 1], lvo[2l])
+        const int lo = 2 * l >= 1 && 2 * l <= nlev ? lvo[2 * l - 1] : 0;
+        const int hi = 2 * l + 1 <= nlev ? lvo[2 * l] : 0;
+        cnt[l] = lo | (hi << 16);
+    }
     __syncthreads();
     // the partners again from the force pass's list (just read: cached), the
     // weights with them
     const size_t base = (size_t)sb * C.nbr_cap;
-    for (int i = tid; i < nb; i += blockDim.x) {
-        const int e0 = rowoff[i], nf = fwd_n[i];
-        const int* srcj = C.fwd_j + sb + i;
-        const T* srcw = C.fwd_w + sb + i;
-        for (int m0 = 0; m0 < nf; m0 += SSA_LOAD_BATCH) {
-            int t[SSA_LOAD_BATCH];
-            T w[SSA_LOAD_BATCH];
-#pragma unroll
-            for (int u = 0; u < SSA_LOAD_BATCH; ++u) {
-                const bool ok = m0 + u < nf;
-                t[u] = ok ? __ldg(srcj + (size_t)(m0 + u) * N) - sb : 0;
-                w[u] = ok ? __ldg(srcw + (size_t)(m0 + u) * N) : T(0);
-            }
-#pragma unroll
-            for (int u = 0; u < SSA_LOAD_BATCH; ++u)
-                if (m0 + u < nf) {
-                    const int pos = atomicAdd(&cnt[ent[e0 + m0 + u]], 1);
-                    V.rec_st[base + pos] = (uint32_t)i | ((uint32_t)min(max(t[u], 0), nb - 1) << 16);
-                    V.rec_w[base + pos] = w[u];
-                }
-        }
-    }
+    struct TW {
+        int t;
+        T w;
+    };
+    ssa_rows_batched(
+        nb, rowoff,
+        [&](int i, int m) {
+            const size_t at = (size_t)m * N + i;
+            return TW{__ldg(fj + at) - sb, __ldg(fw + at)};
+        },
+        [&](int i, int e, const TW& x) {
+            const int pos = cnt_add(cnt, ent[e]);
+            V.rec_st[base + pos] = (uint32_t)i | ((uint32_t)min(max(x.t, 0), nb - 1) << 16);
+            V.rec_w[base + pos] = x.w;
+        });
     if (tid == 0) V.lv_n[d] = nlev;
     return true;
 }
@@ -259,7 +306,7 @@ __device__ bool ssa_sched_domain(const Ctx<T>& C, const SsaDomains& D, const Ssa
 // dense form the blocks loop over the deferred list, and a domain beyond even
 // those capacities gets no schedule (lv_n = -1).
 template <class T>
-__global__ void __launch_bounds__(SCHED_THREADS) k_ssa_sched(Ctx<T> C, SsaDomains D, SsaLevels<T> V, int scap,
+__global__ void __launch_bounds__(SCHED_THREADS, 8) k_ssa_sched(Ctx<T> C, SsaDomains D, SsaLevels<T> V, int scap,
                                                               int ecap, const int* __restrict__ list,
                                                               const int* __restrict__ nlist, int* defer,
                                                               int* ndefer) {
@@ -330,15 +377,18 @@ __device__ __forceinline__ void ssa_exec_levels(const Ctx<T>& C, const SsaLevels
     bool v0 = 0 < nlev && o0 + tid < o1, v1 = 1 < nlev && o1 + tid < o2;
     uint32_t st0 = v0 ? __ldg(rst + o0 + tid) : 0u, st1 = v1 ? __ldg(rst + o1 + tid) : 0u;
     T w0 = v0 ? __ldg(rw + o0 + tid) : T(0), w1 = v1 ? __ldg(rw + o1 + tid) : T(0);
-    vec_t<T> g0 = gauss(st0, w0);
+    vec_t<T> g0{};
+    if (v0) g0 = gauss(st0, w0);
     for (int l = 0; l < nlev; ++l) {
         // record of level l + 2
         const bool v2 = l + 2 < nlev && o2 + tid < o3;
         const uint32_t st2 = v2 ? __ldg(rst + o2 + tid) : 0u;
         const T w2 = v2 ? __ldg(rw + o2 + tid) : T(0);
         const int o4 = lv_start(l + 4);
-        // Gaussian of level l + 1, then the map of level l
-        const vec_t<T> g1 = gauss(st1, w1);
+        // Gaussian of level l + 1 (a warp without a map there skips it), then
+        // the map of level l
+        vec_t<T> g1{};
+        if (v1) g1 = gauss(st1, w1);
         if (v0) apply(st0, g0);
         for (int r = o0 + tid + blockDim.x; r < o1; r += blockDim.x) {
             const uint32_t st = __ldg(rst + r);
