@@ -423,7 +423,8 @@ int dpde_autotune(dpde_handle* h, int32_t scheme, double dt, int32_t steps, dpde
 /* Number of kernel launches in one step of `scheme` (the kernel nodes of
  * the step's CUDA graph, captured here without being run; *launches, host
  * pointer). The count depends on the handle's geometry and tuning: the SSA
- * part has two schedule and two execution launches (ssa_mode 2), or one
+ * part has three schedule and three execution launches (ssa_mode 2: the
+ * regular one and two for domains beyond its capacities), or one
  * launch drawing the Gaussians, then one per non-empty cell colour class
  * (ssa_mode 0, or DPDE_SSA in modes 1 and 2 without the level form) or one
  * for all domains (Hybrid in ssa_mode 1). No device work; the handle's state and step counter are

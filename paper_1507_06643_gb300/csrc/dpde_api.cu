@@ -81,7 +81,10 @@ struct dpde_handle {
     int *lv_off = nullptr, *lv_n = nullptr, *ssa_defer = nullptr;
     int ndom_max = 1;
     struct SsaCaps {
-        int scap_s = 0, ecap_s = 0, scap_sd = 0, ecap_sd = 0, scap_x = 0, scap_xd = 0;
+        // three tiers each: regular (one block per domain), deferred (a few
+        // blocks per SM), large (one block per SM)
+        int scap_s[3] = {0, 0, 0}, ecap_s[3] = {0, 0, 0}, scap_x[3] = {0, 0, 0};
+        int grid_s[3] = {0, 0, 0}, grid_x[3] = {0, 0, 0};
         bool ok = false;   // domains small enough for the level form
     } ssa_caps[2];
     int nsm = 152;
@@ -235,21 +238,30 @@ void enqueue_ssa_levels(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, 
     V.lv_n = h->lv_n;
     V.rec_st = reinterpret_cast<uint32_t*>(h->fwd_g);
     V.rec_w = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(h->fwd_g) + ssa_rec_w_offset(h));
+    // counts: [0, 1] schedule tiers 1, 2; [2, 3] execution tiers 1, 2; then the lists
     int* cnt = h->ssa_defer;
-    int* sdef = cnt + 2;
-    int* xdef = sdef + h->ndom_max;
-    cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st);
+    int* lst[4];
+    for (int k = 0; k < 4; ++k) lst[k] = cnt + 4 + (size_t)k * h->ndom_max;
+    cudaMemsetAsync(cnt, 0, 4 * sizeof(int), st);
     phase(h, st, DPDE_PHASE_SSA_GAUSS, 0);
-    k_ssa_sched<T><<<D.n, SCHED_THREADS, ssa_sched_smem(K.scap_s, K.ecap_s), st>>>(C, D, V, K.scap_s, K.ecap_s,
-                                                                                  nullptr, nullptr, sdef, cnt);
-    k_ssa_sched<T><<<h->nsm, SCHED_THREADS, ssa_sched_smem(K.scap_sd, K.ecap_sd), st>>>(
-        C, D, V, K.scap_sd, K.ecap_sd, sdef, cnt, nullptr, nullptr);
+    for (int t = 0; t < 3; ++t) {
+        const int* in = t == 0 ? nullptr : lst[t - 1];
+        const int* nin = t == 0 ? nullptr : cnt + t - 1;
+        int* out = t < 2 ? lst[t] : nullptr;
+        int* nout = t < 2 ? cnt + t : nullptr;
+        k_ssa_sched<T><<<K.grid_s[t], SCHED_THREADS, ssa_sched_smem(K.scap_s[t], K.ecap_s[t]), st>>>(
+            C, D, V, K.scap_s[t], K.ecap_s[t], in, nin, out, nout);
+    }
     phase(h, st, DPDE_PHASE_SSA_GAUSS, 1);
     phase(h, st, DPDE_PHASE_SSA, 0);
-    k_ssa_exec<T><<<D.n, h->ssa_block, ssa_exec_smem<T>(K.scap_x), st>>>(C, D, V, K.scap_x, nullptr, nullptr, xdef,
-                                                                         cnt + 1, dt, sqrt_dt);
-    k_ssa_exec<T><<<h->nsm, h->ssa_block, ssa_exec_smem<T>(K.scap_xd), st>>>(C, D, V, K.scap_xd, xdef, cnt + 1,
-                                                                             nullptr, nullptr, dt, sqrt_dt);
+    for (int t = 0; t < 3; ++t) {
+        const int* in = t == 0 ? nullptr : lst[2 + t - 1];
+        const int* nin = t == 0 ? nullptr : cnt + 2 + t - 1;
+        int* out = t < 2 ? lst[2 + t] : nullptr;
+        int* nout = t < 2 ? cnt + 2 + t : nullptr;
+        k_ssa_exec<T><<<K.grid_x[t], h->ssa_block, ssa_exec_smem<T>(K.scap_x[t]), st>>>(C, D, V, K.scap_x[t], in,
+                                                                                          nin, out, nout, dt, sqrt_dt);
+    }
     phase(h, st, DPDE_PHASE_SSA, 1);
 }
 
@@ -722,14 +734,17 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     }
     rdom_cell0.push_back((int)ncells);
     // shared-memory capacities of the level form, per domain table (0 bricks,
-    // 1 whole replicas), from the mean domain size M: regular launches hold
-    // M + 5 sqrt(M) + 32 particles (a uniform fluid's domains stay below) for
-    // the execution, 1.3 M + 64 particles and 1.3 M e + 256 entries (e forward
-    // entries per particle at the densest replica's density) for the
-    // schedule; the deferred launches take what ~200 KB hold (the schedule
-    // 16,384 particles). The form is used where no domain is expected above
+    // 1 whole replicas), from the mean domain size M, in three tiers: the
+    // regular launches (a block per domain) hold M + 5 sqrt(M) + 32
+    // particles (a uniform fluid's domains stay below) for the execution,
+    // 1.3 M + 64 particles and 1.2 M e + 256 entries (e forward entries per
+    // particle at the densest replica's density) for the schedule; the
+    // deferred launches (several blocks per SM) ~2.5x that; the last ones
+    // what ~200 KB hold. The form is used where no domain is expected above
     // 16,384 particles.
     {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
         const double e_pp = 2.0 / 3.0 * M_PI * rho_max * P.r_cut * P.r_cut * P.r_cut * 1.15;
         const size_t smem_big = 200 * 1024;
         const size_t per = h->mixed ? (sizeof(float4) + sizeof(ff) + 4) : (sizeof(d4) + sizeof(double) + 4);
@@ -746,12 +761,30 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
                 return std::min(SSA_LOCAL_MAX,
                                 (int)((smem_big - SSA_LV_STRIDE * sizeof(int)) / 2 - (2 * sc + 1)) / 16 * 16);
             };
-            K.scap_s = std::min(16384, up16(1.3 * M + 64));
-            K.ecap_s = std::min(ecap_fit(K.scap_s), up16(1.3 * M * e_pp + 256));
-            K.scap_sd = 16384;
-            K.ecap_sd = ecap_fit(K.scap_sd);
-            K.scap_x = std::min((int)((smem_big - 32) / per), ((int)std::ceil(M + 5.0 * std::sqrt(M) + 32) + 31) / 32 * 32);
-            K.scap_xd = (int)((smem_big - 32) / per);
+            // schedule: 1.3 M particles / 1.2 M e entries; 2.5 M / 6.25 M e (a
+            // brick compressed 2.5-fold holds ~6x the entries) in ~96 KB; the
+            // largest that ~200 KB hold
+            K.scap_s[0] = std::min(16384, up16(1.3 * M + 64));
+            K.ecap_s[0] = std::min(ecap_fit(K.scap_s[0]), up16(1.2 * M * e_pp + 256));
+            K.scap_s[1] = std::min(16384, up16(2.5 * M + 64));
+            K.ecap_s[1] = std::min(ecap_fit(K.scap_s[1]), up16(6.25 * M * e_pp + 256));
+            while (K.ecap_s[1] > K.ecap_s[0] && ssa_sched_smem(K.scap_s[1], K.ecap_s[1]) > smem_big / 2)
+                K.ecap_s[1] = std::max(K.ecap_s[0], K.ecap_s[1] * 7 / 8 / 16 * 16);
+            K.scap_s[2] = 16384;
+            K.ecap_s[2] = ecap_fit(K.scap_s[2]);
+            // execution: M + 5 sqrt(M) + 32 particles; 2.5 M in <= 96 KB; ~200 KB
+            const int xfit = (int)((smem_big - 32) / per);
+            K.scap_x[0] = std::min(xfit, ((int)std::ceil(M + 5.0 * std::sqrt(M) + 32) + 31) / 32 * 32);
+            K.scap_x[1] = std::max(K.scap_x[0], std::min(xfit / 2, ((int)std::ceil(2.5 * M + 64) + 31) / 32 * 32));
+            K.scap_x[2] = xfit;
+            const size_t smem_sm = 227 * 1024;
+            K.grid_s[0] = ndom;
+            K.grid_s[1] = h->nsm * std::max<int>(1, (int)(smem_sm / (ssa_sched_smem(K.scap_s[1], K.ecap_s[1]) + 1024)));
+            K.grid_s[2] = h->nsm;
+            K.grid_x[0] = ndom;
+            const size_t xs1 = h->mixed ? ssa_exec_smem<float>(K.scap_x[1]) : ssa_exec_smem<double>(K.scap_x[1]);
+            K.grid_x[1] = h->nsm * std::max<int>(1, std::min<int>(8, (int)(smem_sm / (xs1 + 1024))));
+            K.grid_x[2] = h->nsm;
             K.ok = biggest <= 16384.0;
         }
     }
@@ -868,16 +901,14 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     h->ndom_max = std::max(1, std::max(h->nbricks, h->R));
     CKC(cudaMalloc(&h->lv_off, sizeof(int) * (size_t)h->ndom_max * SSA_LV_STRIDE));
     CKC(cudaMalloc(&h->lv_n, sizeof(int) * (size_t)h->ndom_max));
-    CKC(cudaMalloc(&h->ssa_defer, sizeof(int) * (2 + 2 * (size_t)h->ndom_max)));
+    CKC(cudaMalloc(&h->ssa_defer, sizeof(int) * (4 + 4 * (size_t)h->ndom_max)));
     {
-        int dev = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
         size_t ms = 0, mx = 0;
-        for (const auto& K : h->ssa_caps) {
-            ms = std::max({ms, ssa_sched_smem(K.scap_s, K.ecap_s), ssa_sched_smem(K.scap_sd, K.ecap_sd)});
-            mx = std::max({mx, h->mixed ? ssa_exec_smem<float>(K.scap_x) : ssa_exec_smem<double>(K.scap_x),
-                           h->mixed ? ssa_exec_smem<float>(K.scap_xd) : ssa_exec_smem<double>(K.scap_xd)});
-        }
+        for (const auto& K : h->ssa_caps)
+            for (int t = 0; t < 3; ++t) {
+                ms = std::max(ms, ssa_sched_smem(K.scap_s[t], K.ecap_s[t]));
+                mx = std::max(mx, h->mixed ? ssa_exec_smem<float>(K.scap_x[t]) : ssa_exec_smem<double>(K.scap_x[t]));
+            }
         const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
         if (h->mixed) {
             CKC(cudaFuncSetAttribute(k_ssa_sched<float>, A, (int)ms));

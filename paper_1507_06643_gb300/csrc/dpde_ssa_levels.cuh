@@ -26,10 +26,11 @@
 //                each pair's Gaussian on the fly (Philox is keyed on the ids),
 //                with a block barrier between levels; writes the state back.
 // Domains too large for the regular shared-memory capacities are deferred to
-// a second launch of each kernel with larger capacities; beyond those, the
-// execution runs on the state in global memory (same levels, same bits), and
-// a domain whose schedule does not fit at all is executed class by class
-// along the colour order itself.
+// a second launch of each kernel with ~2.5x larger capacities (several
+// blocks per SM), and from there to a third with what ~200 KB hold; beyond
+// those, the execution runs on the state in global memory (same levels, same
+// bits), and a domain whose schedule does not fit at all is executed class by
+// class along the colour order itself.
 #pragma once
 
 #include "dpde_kernels.cuh"
@@ -301,28 +302,23 @@ __device__ bool ssa_sched_domain(const Ctx<T>& C, const SsaDomains& D, const Ssa
     return true;
 }
 
-// One launch over the domains: in the regular form (list == nullptr) block d
-// takes domain d and defers a domain beyond its capacities to `defer`; in the
-// dense form the blocks loop over the deferred list, and a domain beyond even
-// those capacities gets no schedule (lv_n = -1).
+// One launch over the domains. Regular form (list == nullptr): block d takes
+// domain d. Deferred form: the blocks loop over `list`. A domain beyond the
+// launch's capacities is passed on to `defer` when one is given, else left
+// without a schedule (lv_n = -1: executed along the colour order).
 template <class T>
 __global__ void __launch_bounds__(SCHED_THREADS, 8) k_ssa_sched(Ctx<T> C, SsaDomains D, SsaLevels<T> V, int scap,
-                                                              int ecap, const int* __restrict__ list,
-                                                              const int* __restrict__ nlist, int* defer,
-                                                              int* ndefer) {
+                                                                 int ecap, const int* __restrict__ list,
+                                                                 const int* __restrict__ nlist, int* defer,
+                                                                 int* ndefer) {
     extern __shared__ __align__(16) unsigned char sched_smem[];
-    if (!list) {
-        const int d = blockIdx.x;
+    const int n = list ? *nlist : (int)gridDim.x;
+    for (int u = blockIdx.x; u < n; u += gridDim.x) {
+        const int d = list ? list[u] : u;
         if (!ssa_sched_domain(C, D, V, d, scap, ecap, sched_smem) && threadIdx.x == 0) {
             V.lv_n[d] = -1;
-            defer[atomicAdd(ndefer, 1)] = d;
+            if (defer) defer[atomicAdd(ndefer, 1)] = d;
         }
-        return;
-    }
-    const int n = *nlist;
-    for (int u = blockIdx.x; u < n; u += gridDim.x) {
-        const int d = list[u];
-        if (!ssa_sched_domain(C, D, V, d, scap, ecap, sched_smem) && threadIdx.x == 0) V.lv_n[d] = -1;
         __syncthreads();
     }
 }
@@ -486,22 +482,18 @@ __device__ void ssa_exec_domain(const Ctx<T>& C, const SsaDomains& D, const SsaL
     }
 }
 
-// Regular form (list == nullptr): block d takes domain d and defers it when
-// it has more than scap particles. Dense form: the blocks loop over `list`,
-// the deferred domains.
+// Regular form (list == nullptr): block d takes domain d. Deferred form: the
+// blocks loop over `list`. A domain with more than scap particles is passed
+// on to `defer` when one is given, else run on the state in global memory.
 template <class T>
 __global__ void __launch_bounds__(SSA_EXEC_THREADS_MAX) k_ssa_exec(Ctx<T> C, SsaDomains D, SsaLevels<T> V,
                                                                     int scap, const int* __restrict__ list,
                                                                     const int* __restrict__ nlist, int* defer,
                                                                     int* ndefer, T dt, T sqrt_dt) {
     extern __shared__ __align__(16) unsigned char exec_smem[];
-    if (!list) {
-        ssa_exec_domain(C, D, V, blockIdx.x, scap, defer, ndefer, dt, sqrt_dt, exec_smem);
-        return;
-    }
-    const int n = *nlist;
+    const int n = list ? *nlist : (int)gridDim.x;
     for (int u = blockIdx.x; u < n; u += gridDim.x) {
-        ssa_exec_domain(C, D, V, list[u], scap, nullptr, nullptr, dt, sqrt_dt, exec_smem);
+        ssa_exec_domain(C, D, V, list ? list[u] : u, scap, defer, ndefer, dt, sqrt_dt, exec_smem);
         __syncthreads();
     }
 }

@@ -398,10 +398,11 @@ def test_ssa_launches_follow_colour_classes(box, bricks):
     S.set_tuning(ssa_mode=1)
     assert S.step_launches("HYBRID") - ser == 2
     assert S.step_launches("SSA") == ssa
-    # level form: two schedule and two execution launches, for bricks and whole replicas
+    # level form: three schedule and three execution launches (the regular one
+    # and two for deferred domains), for bricks and whole replicas
     S.set_tuning(ssa_mode=2)
-    assert S.step_launches("HYBRID") - ser == 4
-    assert S.step_launches("SSA") - (ser - 1) == 4
+    assert S.step_launches("HYBRID") - ser == 6
+    assert S.step_launches("SSA") - (ser - 1) == 6
     S.close()
 
 
@@ -586,27 +587,31 @@ def test_ssa_modes_agree_on_thin_and_batched_boxes(scheme):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("case", ["dense_brick", "global_state", "no_schedule"])
+@pytest.mark.parametrize("case", ["dense_brick", "denser_brick", "densest_brick", "global_state", "no_schedule"])
 def test_ssa_level_form_fallbacks_agree_bit_for_bit(precision, case):
     """The level form's paths beyond its regular shared-memory capacities give
     the colour order's bits: a brick holding more particles than the regular
-    execution stages (deferred to the launch with larger capacities); one
-    domain too large for any staging (levels run on the state in global
-    memory); one domain with more forward entries than a schedule holds (run
-    class by class along the colour order)."""
+    execution stages (deferred to the launch with ~2.5x the capacity), one
+    denser still (both kernels deferred once), one beyond 2.5x the mean
+    (both deferred to the largest tier); one domain too large for any
+    staging (levels run on the state in global memory); one domain with more
+    forward entries than a schedule holds (run class by class along the
+    colour order)."""
     from paper_1507_06643_gb300 import dpde
     rng = np.random.default_rng(41)
-    if case == "dense_brick":
+    if case in ("dense_brick", "denser_brick", "densest_brick"):
         n0, L, bricks = 4000, cube(4000), (2, 2, 2)
         q, p, e = make_state([(n0, (L,) * 3, 50.0, 1.0, bricks)], 42, precision == "mixed")
-        extra = 0.25 * L + rng.uniform(-2.0, 2.0, (300, 3))   # inside brick (0, 0, 0), density ~8 there
+        extra_n, half = {"dense_brick": (300, 2.0), "denser_brick": (1000, 0.49 * L / 2),
+                         "densest_brick": (1600, 0.49 * L / 2)}[case]
+        extra = 0.25 * L + rng.uniform(-half, half, (extra_n, 3))   # inside brick (0, 0, 0)
         q = np.vstack([q, extra])
-        p = np.vstack([p, rng.standard_normal((300, 3))])
-        e = np.concatenate([e, 50.0 * (1 + 0.05 * rng.uniform(-1, 1, 300))])
+        p = np.vstack([p, rng.standard_normal((extra_n, 3))])
+        e = np.concatenate([e, 50.0 * (1 + 0.05 * rng.uniform(-1, 1, extra_n))])
         if precision == "mixed":
             q = q.astype(np.float32).astype(np.float64)
             p = p.astype(np.float32).astype(np.float64)
-        n = n0 + 300
+        n = n0 + extra_n
     else:
         n = 8000 if case == "global_state" else 15000
         L, bricks = cube(n), (1, 1, 1)
