@@ -243,25 +243,33 @@ void enqueue_ssa_levels(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, 
     int* lst[4];
     for (int k = 0; k < 4; ++k) lst[k] = cnt + 4 + (size_t)k * h->ndom_max;
     cudaMemsetAsync(cnt, 0, 4 * sizeof(int), st);
+    auto sched_tiers = [&]() {
+        for (int t = 1; t < 3; ++t)
+            k_ssa_sched<T><<<K.grid_s[t], SCHED_THREADS, ssa_sched_smem(K.scap_s[t], K.ecap_s[t]), st>>>(
+                C, D, V, K.scap_s[t], K.ecap_s[t], 0, lst[t - 1], cnt + t - 1, t < 2 ? lst[t] : nullptr,
+                t < 2 ? cnt + t : nullptr);
+    };
+    auto exec_tiers = [&]() {
+        for (int t = 1; t < 3; ++t)
+            k_ssa_exec<T><<<K.grid_x[t], h->ssa_block, ssa_exec_smem<T>(K.scap_x[t]), st>>>(
+                C, D, V, K.scap_x[t], 0, lst[2 + t - 1], cnt + 2 + t - 1, t < 2 ? lst[2 + t] : nullptr,
+                t < 2 ? cnt + 2 + t : nullptr, dt, sqrt_dt);
+    };
+    auto sched_regular = [&](cudaStream_t s, int d0, int n) {
+        k_ssa_sched<T><<<n, SCHED_THREADS, ssa_sched_smem(K.scap_s[0], K.ecap_s[0]), s>>>(
+            C, D, V, K.scap_s[0], K.ecap_s[0], d0, nullptr, nullptr, lst[0], cnt);
+    };
+    auto exec_regular = [&](cudaStream_t s, int d0, int n) {
+        k_ssa_exec<T><<<n, h->ssa_block, ssa_exec_smem<T>(K.scap_x[0]), s>>>(C, D, V, K.scap_x[0], d0, nullptr,
+                                                                             nullptr, lst[2], cnt + 2, dt, sqrt_dt);
+    };
     phase(h, st, DPDE_PHASE_SSA_GAUSS, 0);
-    for (int t = 0; t < 3; ++t) {
-        const int* in = t == 0 ? nullptr : lst[t - 1];
-        const int* nin = t == 0 ? nullptr : cnt + t - 1;
-        int* out = t < 2 ? lst[t] : nullptr;
-        int* nout = t < 2 ? cnt + t : nullptr;
-        k_ssa_sched<T><<<K.grid_s[t], SCHED_THREADS, ssa_sched_smem(K.scap_s[t], K.ecap_s[t]), st>>>(
-            C, D, V, K.scap_s[t], K.ecap_s[t], in, nin, out, nout);
-    }
+    sched_regular(st, 0, D.n);
+    sched_tiers();
     phase(h, st, DPDE_PHASE_SSA_GAUSS, 1);
     phase(h, st, DPDE_PHASE_SSA, 0);
-    for (int t = 0; t < 3; ++t) {
-        const int* in = t == 0 ? nullptr : lst[2 + t - 1];
-        const int* nin = t == 0 ? nullptr : cnt + 2 + t - 1;
-        int* out = t < 2 ? lst[2 + t] : nullptr;
-        int* nout = t < 2 ? cnt + 2 + t : nullptr;
-        k_ssa_exec<T><<<K.grid_x[t], h->ssa_block, ssa_exec_smem<T>(K.scap_x[t]), st>>>(C, D, V, K.scap_x[t], in,
-                                                                                          nin, out, nout, dt, sqrt_dt);
-    }
+    exec_regular(st, 0, D.n);
+    exec_tiers();
     phase(h, st, DPDE_PHASE_SSA, 1);
 }
 

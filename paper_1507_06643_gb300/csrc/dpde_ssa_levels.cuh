@@ -41,7 +41,7 @@ constexpr int SSA_MAXLEV = 1023;         // levels of one domain kept by the sch
 constexpr int SSA_LV_STRIDE = SSA_MAXLEV + 2;
 constexpr int SCHED_THREADS = 128;
 constexpr int SSA_LOAD_BATCH = 8;       // entries of a row taken together by the level walk
-constexpr int SSA_ROW_BATCH = 4;        // entries per particle, two particles, loaded together
+constexpr int SSA_COL_BATCH = 6;        // particles whose m-th entries a thread loads together
 constexpr int SSA_EXEC_THREADS_MAX = 128;
 constexpr int SSA_LOCAL_MAX = 65535;      // particles (and entries) of one domain: 16-bit local indices
 
@@ -116,31 +116,32 @@ __device__ __forceinline__ int cnt_add(int* cnt, int l) {
 }
 __device__ __forceinline__ int cnt_get(const int* cnt, int l) { return (cnt[l >> 1] >> ((l & 1) << 4)) & 0xffff; }
 
-// The rows of the domain's particles, two particles per thread at a time
-// (i and i + blockDim), the entries of both loaded together in chunks of
-// SSA_ROW_BATCH: f(i, e, m, k) is called for the k-th value of entry m of
-// particle i, whose row starts at rowoff[i] (e = rowoff[i] + m), with the
-// values loaded by load(i, m).
+// The forward entries of the domain's particles, entry index m outermost:
+// a thread takes SSA_COL_BATCH particles i = i0 + tid + k blockDim (so a
+// warp's lanes read consecutive words of each entry row [m N + i]) and, for
+// every m below their row lengths, issues the loads of all of them before
+// using them. use(i, e, v) gets the value load(i, m) of entry m of particle
+// i, whose row starts at rowoff[i] (e = rowoff[i] + m).
 template <class Load, class Use>
-__device__ __forceinline__ void ssa_rows_batched(int nb, const unsigned short* rowoff, Load&& load, Use&& use) {
+__device__ __forceinline__ void ssa_rows_mmajor(int nb, const unsigned short* rowoff, Load&& load, Use&& use) {
     const int bd = blockDim.x;
-    for (int i0 = threadIdx.x; i0 < nb; i0 += 2 * bd) {
-        const int i1 = i0 + bd;
-        const int a0 = rowoff[i0], na = rowoff[i0 + 1] - a0;
-        const int b0 = i1 < nb ? rowoff[i1] : 0, nbv = i1 < nb ? rowoff[i1 + 1] - b0 : 0;
-        const int nmax = max(na, nbv);
-        for (int m0 = 0; m0 < nmax; m0 += SSA_ROW_BATCH) {
-            decltype(load(0, 0)) va[SSA_ROW_BATCH], vb[SSA_ROW_BATCH];
+    for (int i0 = 0; i0 < nb; i0 += SSA_COL_BATCH * bd) {
+        int e0[SSA_COL_BATCH], nf[SSA_COL_BATCH], mx = 0;
 #pragma unroll
-            for (int u = 0; u < SSA_ROW_BATCH; ++u) {
-                if (m0 + u < na) va[u] = load(i0, m0 + u);
-                if (m0 + u < nbv) vb[u] = load(i1, m0 + u);
-            }
+        for (int k = 0; k < SSA_COL_BATCH; ++k) {
+            const int i = i0 + (int)threadIdx.x + k * bd;
+            e0[k] = i < nb ? rowoff[i] : 0;
+            nf[k] = i < nb ? rowoff[i + 1] - e0[k] : 0;
+            mx = max(mx, nf[k]);
+        }
+        for (int m = 0; m < mx; ++m) {
+            decltype(load(0, 0)) v[SSA_COL_BATCH];
 #pragma unroll
-            for (int u = 0; u < SSA_ROW_BATCH; ++u) {
-                if (m0 + u < na) use(i0, a0 + m0 + u, va[u]);
-                if (m0 + u < nbv) use(i1, b0 + m0 + u, vb[u]);
-            }
+            for (int k = 0; k < SSA_COL_BATCH; ++k)
+                if (m < nf[k]) v[k] = load(i0 + (int)threadIdx.x + k * bd, m);
+#pragma unroll
+            for (int k = 0; k < SSA_COL_BATCH; ++k)
+                if (m < nf[k]) use(i0 + (int)threadIdx.x + k * bd, e0[k] + m, v[k]);
         }
     }
 }
@@ -178,7 +179,7 @@ __device__ bool ssa_sched_domain(const Ctx<T>& C, const SsaDomains& D, const Ssa
     const int* fj = C.fwd_j + sb;   // entry m of local particle i at fj[m N + i]
     const T* fw = C.fwd_w + sb;
     // 2. partner slots, local
-    ssa_rows_batched(
+    ssa_rows_mmajor(
         nb, rowoff, [&](int i, int m) { return __ldg(fj + (size_t)m * N + i) - sb; },
         [&](int, int e, int t) {
             if ((unsigned)t >= (unsigned)nb) s_flag = 1;   // never by construction
@@ -287,7 +288,7 @@ __device__ bool ssa_sched_domain(const Ctx<T>& C, const SsaDomains& D, const Ssa
         int t;
         T w;
     };
-    ssa_rows_batched(
+    ssa_rows_mmajor(
         nb, rowoff,
         [&](int i, int m) {
             const size_t at = (size_t)m * N + i;
@@ -302,21 +303,24 @@ __device__ bool ssa_sched_domain(const Ctx<T>& C, const SsaDomains& D, const Ssa
     return true;
 }
 
-// One launch over the domains. Regular form (list == nullptr): block d takes
-// domain d. Deferred form: the blocks loop over `list`. A domain beyond the
-// launch's capacities is passed on to `defer` when one is given, else left
-// without a schedule (lv_n = -1: executed along the colour order).
+// One launch over the domains. Regular form (list == nullptr): block u takes
+// domain d0 + u. Deferred form: the blocks loop over `list`. A domain beyond
+// the launch's capacities is passed on to `defer` when one is given (lv_n =
+// SSA_PENDING until a later launch schedules it), else left without a
+// schedule (lv_n = -1: executed along the colour order).
+constexpr int SSA_PENDING = -2;
+
 template <class T>
 __global__ void __launch_bounds__(SCHED_THREADS, 8) k_ssa_sched(Ctx<T> C, SsaDomains D, SsaLevels<T> V, int scap,
-                                                                 int ecap, const int* __restrict__ list,
+                                                                 int ecap, int d0, const int* __restrict__ list,
                                                                  const int* __restrict__ nlist, int* defer,
                                                                  int* ndefer) {
     extern __shared__ __align__(16) unsigned char sched_smem[];
     const int n = list ? *nlist : (int)gridDim.x;
     for (int u = blockIdx.x; u < n; u += gridDim.x) {
-        const int d = list ? list[u] : u;
+        const int d = list ? list[u] : d0 + u;
         if (!ssa_sched_domain(C, D, V, d, scap, ecap, sched_smem) && threadIdx.x == 0) {
-            V.lv_n[d] = -1;
+            V.lv_n[d] = defer ? SSA_PENDING : -1;
             if (defer) defer[atomicAdd(ndefer, 1)] = d;
         }
         __syncthreads();
@@ -454,7 +458,11 @@ __device__ void ssa_exec_domain(const Ctx<T>& C, const SsaDomains& D, const SsaL
     if (nb == 0) return;
     const int nlev = V.lv_n[d];
     const int rep = C.rep_of_cell[D.cell0[d]];
-    if (nlev < 0) {   // no schedule, even with the dense capacities: the colour order itself
+    if (nlev == SSA_PENDING && defer) {   // its schedule comes from a later launch
+        if (threadIdx.x == 0) defer[atomicAdd(ndefer, 1)] = d;
+        return;
+    }
+    if (nlev < 0) {   // no schedule, even with the largest capacities: the colour order itself
         ssa_exec_classes(C, D, d, rep, dt, sqrt_dt);
         return;
     }
@@ -482,18 +490,19 @@ __device__ void ssa_exec_domain(const Ctx<T>& C, const SsaDomains& D, const SsaL
     }
 }
 
-// Regular form (list == nullptr): block d takes domain d. Deferred form: the
-// blocks loop over `list`. A domain with more than scap particles is passed
-// on to `defer` when one is given, else run on the state in global memory.
+// Regular form (list == nullptr): block u takes domain d0 + u. Deferred
+// form: the blocks loop over `list`. A domain with more than scap particles,
+// or whose schedule is still pending, is passed on to `defer` when one is
+// given, else run on the state in global memory.
 template <class T>
 __global__ void __launch_bounds__(SSA_EXEC_THREADS_MAX) k_ssa_exec(Ctx<T> C, SsaDomains D, SsaLevels<T> V,
-                                                                    int scap, const int* __restrict__ list,
+                                                                    int scap, int d0, const int* __restrict__ list,
                                                                     const int* __restrict__ nlist, int* defer,
                                                                     int* ndefer, T dt, T sqrt_dt) {
     extern __shared__ __align__(16) unsigned char exec_smem[];
     const int n = list ? *nlist : (int)gridDim.x;
     for (int u = blockIdx.x; u < n; u += gridDim.x) {
-        ssa_exec_domain(C, D, V, list ? list[u] : u, scap, defer, ndefer, dt, sqrt_dt, exec_smem);
+        ssa_exec_domain(C, D, V, list ? list[u] : d0 + u, scap, defer, ndefer, dt, sqrt_dt, exec_smem);
         __syncthreads();
     }
 }
