@@ -140,7 +140,10 @@ extern "C" {
 #define DPDE_ERR_NEG_EPS       -4  /* some eps_i <= 0 after the last step(s);
                                       the state was advanced, nothing clamped */
 #define DPDE_ERR_NONFINITE     -5  /* NaN/Inf in the state                    */
-#define DPDE_ERR_TIMEOUT       -6  /* a bounded device wait gave up           */
+#define DPDE_ERR_TIMEOUT       -6  /* a bounded device wait gave up: a grid
+                                      barrier of the persistent SSA launch
+                                      (ssa_mode 3) waited past the handle's
+                                      wait budget; the step is incomplete     */
 #define DPDE_ERR_CAPACITY      -7  /* a particle had more neighbours than the
                                       list holds (density far above the one
                                       the handle was sized for); the step's
@@ -393,13 +396,27 @@ typedef struct dpde_tuning {
                          /* which each warp takes whole domains and walks their       */
                          /* colour classes in order (domains share no chain, so their */
                          /* sequences commute), the domains' state staged in shared   */
-                         /* memory where it fits                                      */
+                         /* memory where it fits; 3: the classes of mode 0 in one     */
+                         /* persistent cooperative launch (a grid sized to full       */
+                         /* co-residency), the blocks meeting at a grid barrier       */
+                         /* between classes whose wait is bounded by the handle's     */
+                         /* wait budget (dpde_set_wait_budget)                        */
     int32_t ssa_group;   /* domains per warp of ssa_mode 1, 1..8; 0 = automatic (32 /  */
                          /* the most cells of one class in one domain); get_tuning     */
                          /* reports the value in use                                   */
     int32_t reserved;    /* must be 0                                                  */
     double ms_per_step;  /* dpde_autotune: measured ms per step of the result; else 0  */
 } dpde_tuning;
+
+/* Wait budget of the grid barriers of the persistent SSA launch (ssa_mode
+ * 3), in GPU clock cycles (default 2e9, about a second at 2 GHz): a block
+ * that waits longer at a barrier raises a status and leaves, every other
+ * block leaves at its next barrier, and the next dpde_sync returns
+ * DPDE_ERR_TIMEOUT (the step's SSA part is then incomplete; set a state
+ * again). 0 makes every block that has to wait give up at once. Waits for
+ * the handle's stream and drops the captured step graphs. DPDE_ERR_ARG for
+ * cycles < 0. */
+int dpde_set_wait_budget(dpde_handle* h, int64_t cycles);
 
 /* Current tuning of the handle (host pointer). */
 int dpde_get_tuning(dpde_handle* h, dpde_tuning* out);

@@ -2,6 +2,7 @@
 // sequence of one timestep, CUDA-graph replay, observables, diagnostics.
 #include "dpde.h"
 #include "dpde_ssa_levels.cuh"
+#include "dpde_ssa_persistent.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -88,6 +89,11 @@ struct dpde_handle {
         bool ok = false;   // domains small enough for the level form
     } ssa_caps[2];
     int nsm = 152;
+    // the persistent per-class SSA launch (ssa_mode 3): class offsets on the
+    // device, its grid barrier and the barrier's wait budget (clock cycles)
+    int* d_col_off[2] = {nullptr, nullptr};
+    GridBarrier* d_bar = nullptr;
+    long long wait_budget = 2000000000ll;
     int ssa_group = 0;        // bricks per warp; 0 = dom_group_auto
     int dom_group_auto = 1;   // 32 / the largest class of a brick, in 1..SSA_GROUP_MAX
     int hcap = 0;             // halo particles staged per force tile
@@ -302,6 +308,27 @@ void enqueue_ssa(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_
         phase(h, st, DPDE_PHASE_SSA, 1);
         return;
     }
+    if (h->ssa_mode == 3) {
+        // one cooperative launch over all classes, a grid barrier between them
+        const size_t smem = ssa_smem_bytes(h->ssa_block);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ssa_persistent<T>, h->ssa_block, smem);
+        cudaMemsetAsync(h->d_bar, 0, sizeof(GridBarrier), st);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)std::max(1, per_sm * h->nsm));
+        cfg.blockDim = dim3((unsigned)h->ssa_block);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_ssa_persistent<T>, C, (const int*)h->col_cells[whole],
+                           (const int*)h->d_col_off[whole], dt, sqrt_dt, h->d_bar, h->wait_budget);
+        phase(h, st, DPDE_PHASE_SSA, 1);
+        return;
+    }
     for (int k = 0; k < NCOLOURS; ++k) {
         const int n = off[k + 1] - off[k];
         if (n > 0)
@@ -446,6 +473,9 @@ int read_status(dpde_handle* h) {
     CK(h, cudaMemcpyAsync(&st, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    if (st & ST_TIMEOUT)
+        return fail(h, DPDE_ERR_TIMEOUT, "a grid barrier of the persistent SSA launch waited past its budget; "
+                                         "the step's state is incomplete");
     if (st & ST_CAPACITY) return fail(h, DPDE_ERR_CAPACITY, "neighbour list capacity exceeded");
     if (st & ST_WALL) return fail(h, DPDE_ERR_ARG, "the moving wall reached the lowest cell layer");
     if (st & ST_DOMAIN) return fail(h, DPDE_ERR_CUDA, "internal error: an SSA chain left its domain");
@@ -461,7 +491,7 @@ void free_all(dpde_handle* h) {
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
     void* bufs[] = {h->qA, h->pA, h->qB, h->pB, h->F, h->dp, h->upot, h->proj_e0, h->proj_shift, h->proj_partial, h->eA, h->eB, h->nbr_w, h->cA, h->cB, h->nbr_j,
-                    h->nbr_n, h->fwd_j, h->fwd_w, h->fwd_g, h->fwd_n, h->tile_org, h->tile_dim, h->defer, h->col_cells[0], h->col_cells[1], h->dom_cells, h->dom_off, h->dom_cell0, h->rdom_cells, h->rdom_off, h->rdom_cell0, h->lv_off, h->lv_n, h->ssa_defer, h->wallpos, h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
+                    h->nbr_n, h->fwd_j, h->fwd_w, h->fwd_g, h->fwd_n, h->tile_org, h->tile_dim, h->defer, h->col_cells[0], h->col_cells[1], h->dom_cells, h->dom_off, h->dom_cell0, h->rdom_cells, h->rdom_off, h->rdom_cell0, h->lv_off, h->lv_n, h->ssa_defer, h->d_col_off[0], h->d_col_off[1], h->d_bar, h->wallpos, h->idB, h->key, h->tmp, h->cnt, h->start, h->bsum, h->rep_of_slot,
                     h->rep_of_cell, h->brick_rep, h->tab, h->chunk_rep, h->chunk_begin, h->chunk_end,
                     h->rep_chunk_begin, h->partial, h->obs_out, h->d_reps, h->d_step, h->d_status,
                     h->staging, h->cells_out};
@@ -930,7 +960,11 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         CKC(cudaFuncSetAttribute(k_ssa_domains<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SSA_DOMAIN_SMEM));
     else
         CKC(cudaFuncSetAttribute(k_ssa_domains<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, SSA_DOMAIN_SMEM));
+    CKC(cudaMalloc(&h->d_bar, sizeof(GridBarrier)));
+    CKC(cudaMemset(h->d_bar, 0, sizeof(GridBarrier)));
     for (int m = 0; m < 2; ++m) {
+        CKC(cudaMalloc(&h->d_col_off[m], sizeof(int) * (NCOLOURS + 1)));
+        CKC(cudaMemcpy(h->d_col_off[m], h->col_off[m].data(), sizeof(int) * (NCOLOURS + 1), cudaMemcpyHostToDevice));
         CKC(cudaMalloc(&h->col_cells[m], sizeof(int) * c1));
         if (!col_cells[m].empty())
             CKC(cudaMemcpy(h->col_cells[m], col_cells[m].data(), sizeof(int) * col_cells[m].size(),
@@ -1055,6 +1089,16 @@ int dpde_set_projection(dpde_handle* h, int32_t enable, const double* E0) {
     return DPDE_OK;
 }
 
+int dpde_set_wait_budget(dpde_handle* h, int64_t cycles) {
+    if (!h) return DPDE_ERR_ARG;
+    if (cycles < 0) return fail(h, DPDE_ERR_ARG, "the wait budget must be >= 0 clock cycles");
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    h->wait_budget = cycles;
+    return DPDE_OK;
+}
+
 int dpde_get_tuning(dpde_handle* h, dpde_tuning* out) {
     if (!h || !out) return DPDE_ERR_ARG;
     out->tile_edge = h->tile_edge;
@@ -1071,7 +1115,7 @@ int dpde_set_tuning(dpde_handle* h, const dpde_tuning* t) {
     if (!h || !t) return DPDE_ERR_ARG;
     if (t->tile_edge < 2 || t->tile_edge > TILE_EDGE_MAX || t->block < 64 || t->block > 1024 ||
         t->block % 32 != 0 || t->ssa_block < 32 || t->ssa_block > SSA_THREADS_MAX || t->ssa_block % 32 != 0 ||
-        (t->ssa_mode < 0 || t->ssa_mode > 2) || t->ssa_group < 0 || t->ssa_group > SSA_GROUP_MAX ||
+        (t->ssa_mode < 0 || t->ssa_mode > 3) || t->ssa_group < 0 || t->ssa_group > SSA_GROUP_MAX ||
         t->reserved != 0)
         return fail(h, DPDE_ERR_ARG, "tuning out of range");
     CK(h, cudaStreamSynchronize(h->stream));
@@ -1157,9 +1201,9 @@ int dpde_autotune(dpde_handle* h, int32_t scheme, double dt, int32_t steps, dpde
         double best_ms = 0.0;
         if ((rc = trial(best, best_ms)) != DPDE_OK) break;
         const int edges[] = {4, 5, 6, 7, 8}, blocks[] = {128, 256, 512}, ssa_blocks[] = {32, 64, 128},
-                  modes[] = {2, 1, 0}, groups[] = {1, 2, 3, 4};
+                  modes[] = {2, 1, 0, 3}, groups[] = {1, 2, 3, 4};
         const int* cands[] = {edges, blocks, ssa_blocks, modes, groups};
-        const int ncands[] = {5, 3, 3, 3, 4};
+        const int ncands[] = {5, 3, 3, 4, 4};
         for (int stage = 0; stage < 5 && rc == DPDE_OK; ++stage) {
             // bricks per warp matter only to the per-brick SSA launch
             if (stage == 4 && (best.ssa_mode != 1 || scheme != DPDE_HYBRID)) break;

@@ -272,6 +272,8 @@ template <class T>
 __device__ __forceinline__ T pair_pot_at_zero(const PotT<T>& P) { return P.kind == 1 ? T(0) : P.half_arc; }
 
 // Status bits raised by the kernels (read and cleared by the host).
-enum : unsigned int { ST_NEG_EPS = 1u, ST_NONFINITE = 2u, ST_CAPACITY = 4u, ST_DOMAIN = 8u, ST_WALL = 16u };
+enum : unsigned int {
+    ST_NEG_EPS = 1u, ST_NONFINITE = 2u, ST_CAPACITY = 4u, ST_DOMAIN = 8u, ST_WALL = 16u, ST_TIMEOUT = 32u
+};
 
 }  // namespace dpde

@@ -76,7 +76,7 @@ EXPORTS = ["dpde_create", "dpde_set_state", "dpde_get_state", "dpde_step", "dpde
            "dpde_debug_philox", "dpde_debug_gaussian", "dpde_step_profiled", "dpde_get_cells",
            "dpde_checkpoint", "dpde_restore", "dpde_observables_noalloc", "dpde_noalloc_last_error",
            "dpde_step_launches", "dpde_get_tuning", "dpde_set_tuning", "dpde_autotune",
-           "dpde_set_projection"]
+           "dpde_set_projection", "dpde_set_wait_budget"]
 PHASES = ["kick_drift", "scan", "gather", "force", "ssa", "sweep1", "sweep2", "other", "ssa_gauss"]
 
 
@@ -111,6 +111,7 @@ def lib():
         L.dpde_step_launches.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64)]
         L.dpde_get_tuning.argtypes = [vp, C.POINTER(dpde_tuning)]
         L.dpde_set_projection.argtypes = [vp, C.c_int32, C.POINTER(C.c_double)]
+        L.dpde_set_wait_budget.argtypes = [vp, C.c_int64]
         L.dpde_set_tuning.argtypes = [vp, C.POINTER(dpde_tuning)]
         L.dpde_autotune.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, C.POINTER(dpde_tuning)]
         L.dpde_step_profiled.argtypes = [vp, C.c_int64, C.c_double, C.c_int32, dp]
@@ -256,6 +257,10 @@ def dpde_observables_noalloc(params: dpde_params, replica: dpde_replica, q, p, e
     if rc not in (DPDE_OK, DPDE_ERR_NEG_EPS, DPDE_ERR_NONFINITE):
         raise DPDEError(rc, lib().dpde_noalloc_last_error().decode())
     return rc, out.as_dict()
+
+
+def dpde_set_wait_budget(h, cycles: int):
+    return _check(h, lib().dpde_set_wait_budget(h, int(cycles)))
 
 
 def dpde_destroy(h):

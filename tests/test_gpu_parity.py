@@ -151,7 +151,7 @@ def test_walled_ssa_forms_agree_bit_for_bit(precision):
     specs = [(1500, (7.0, 7.0, 10.3), 50.0, 1.0, (1, 1, 3)), (800, (5.5, 5.5, 9.1), 50.0, 1.0, (1, 1, 1))]
     q, p, e = make_state(specs, 64, precision == "mixed")
     outs = []
-    for mode in (0, 1, 2):
+    for mode in (0, 1, 2, 3):
         S = dpde.System(dpde.make_params(precision=precision),
                         [dpde.make_replica(n, box, cv, br, 1, -0.7) for n, box, cv, _, br in specs])
         S.set_tuning(ssa_mode=mode)
@@ -403,6 +403,10 @@ def test_ssa_launches_follow_colour_classes(box, bricks):
     S.set_tuning(ssa_mode=2)
     assert S.step_launches("HYBRID") - ser == 6
     assert S.step_launches("SSA") - (ser - 1) == 6
+    # persistent form: the Gaussian pass and one cooperative launch over all classes
+    S.set_tuning(ssa_mode=3)
+    assert S.step_launches("HYBRID") - ser == 2
+    assert S.step_launches("SSA") - (ser - 1) == 2
     S.close()
 
 
@@ -556,7 +560,8 @@ def test_ssa_modes_agree_bit_for_bit(precision, scheme):
     for t in ({"ssa_mode": 1}, {"ssa_mode": 1, "ssa_block": 32}, {"ssa_mode": 1, "ssa_block": 128},
               {"ssa_mode": 1, "ssa_group": 1}, {"ssa_mode": 1, "ssa_group": 3},
               {"ssa_mode": 1, "ssa_group": 8, "ssa_block": 96},
-              {"ssa_mode": 2}, {"ssa_mode": 2, "ssa_block": 32}, {"ssa_mode": 2, "ssa_block": 128}):
+              {"ssa_mode": 2}, {"ssa_mode": 2, "ssa_block": 32}, {"ssa_mode": 2, "ssa_block": 128},
+              {"ssa_mode": 3}, {"ssa_mode": 3, "ssa_block": 32}, {"ssa_mode": 3, "ssa_block": 128}):
         got = _run_tuned(precision, t, scheme=scheme)
         for a, b in zip(ref, got):
             assert np.array_equal(a, b), t
@@ -572,7 +577,7 @@ def test_ssa_modes_agree_on_thin_and_batched_boxes(scheme):
              (2000, (4.1, 9.0, 16.5), 80.0, 1.0, (1, 3, 1))]
     q, p, e = make_state(specs, 91, True)
     outs = []
-    for mode, group in ((0, 0), (1, 0), (1, 2), (1, 5), (2, 0)):
+    for mode, group in ((0, 0), (1, 0), (1, 2), (1, 5), (2, 0), (3, 0)):
         S = dpde.System(dpde.make_params(precision="mixed"),
                         [dpde.make_replica(n, box, cv, br) for n, box, cv, _, br in specs])
         S.set_tuning(ssa_mode=mode, ssa_group=group)
@@ -648,7 +653,7 @@ def test_autotune_keeps_the_state():
     step0 = dpde.dpde_get_step(S.h)
     t = S.autotune("HYBRID", 0.01, 2)
     assert t["tile_edge"] in (4, 5, 6, 7, 8) and t["block"] in (128, 256, 512)
-    assert t["ssa_block"] in (32, 64, 128) and t["ssa_mode"] in (0, 1, 2) and t["ms_per_step"] > 0
+    assert t["ssa_block"] in (32, 64, 128) and t["ssa_mode"] in (0, 1, 2, 3) and t["ms_per_step"] > 0
     assert 1 <= t["ssa_group"] <= 8
     assert S.tuning()["tile_edge"] == t["tile_edge"]
     after = S.get_state()
@@ -674,7 +679,7 @@ def test_bad_tuning_rejected():
     from paper_1507_06643_gb300 import dpde
     S = dpde.System(dpde.make_params(precision="mixed"), [dpde.make_replica(300, (cube(300),) * 3, 50.0)])
     for kw in ({"tile_edge": 1}, {"tile_edge": 9}, {"block": 48}, {"block": 2048}, {"ssa_block": 256},
-               {"ssa_block": 48}, {"ssa_mode": 3}, {"ssa_mode": -1}, {"ssa_group": 9}, {"ssa_group": -1}):
+               {"ssa_block": 48}, {"ssa_mode": 4}, {"ssa_mode": -1}, {"ssa_group": 9}, {"ssa_group": -1}):
         with pytest.raises(dpde.DPDEError):
             S.set_tuning(**kw)
     S.close()
@@ -728,6 +733,42 @@ def test_neighbour_list_overflow_reported(precision, scheme):
     S.step(2, 0.01, scheme)
     assert S.sync() == dpde.DPDE_OK
     S.close()
+
+
+@pytest.mark.parametrize("scheme", ["SSA", "HYBRID"])
+def test_persistent_ssa_barrier_timeout_reported(scheme):
+    """The persistent SSA launch (ssa_mode 3) bounds the wait of its grid
+    barriers: with a wait budget of 0 cycles every block that reaches a
+    barrier before the last one gives up at once, the launch ends, and
+    dpde_sync reports DPDE_ERR_TIMEOUT; the context stays usable, and with
+    the default budget restored the same steps run clean."""
+    from paper_1507_06643_gb300 import dpde
+    n = 20000
+    L = cube(n)
+    specs = [(n, (L,) * 3, 50.0, 1.0, (2, 2, 2))]
+    q, p, e = make_state(specs, 33, True)
+    S = dpde.System(dpde.make_params(precision="mixed"), [dpde.make_replica(n, (L,) * 3, 50.0, (2, 2, 2))])
+    S.set_tuning(ssa_mode=3)
+    S.set_state(q, p, e)
+    dpde.dpde_set_wait_budget(S.h, 0)
+    S.step(1, 0.01, scheme)
+    assert S.sync() == dpde.DPDE_ERR_TIMEOUT
+    assert "budget" in dpde.lib().dpde_last_error(S.h).decode()
+    with pytest.raises(dpde.DPDEError):
+        dpde.dpde_set_wait_budget(S.h, -1)
+    dpde.dpde_set_wait_budget(S.h, 2_000_000_000)
+    S.set_state(q, p, e)
+    S.step(3, 0.01, scheme)
+    assert S.sync() == dpde.DPDE_OK
+    got = S.get_state()
+    S.close()
+    R = dpde.System(dpde.make_params(precision="mixed"), [dpde.make_replica(n, (L,) * 3, 50.0, (2, 2, 2))])
+    R.set_tuning(ssa_mode=0)
+    R.set_state(q, p, e)
+    R.step(3, 0.01, scheme)
+    for a, b in zip(got, R.get_state()):
+        assert np.array_equal(a, b)
+    R.close()
 
 
 # ---- the benchmark's workload at full size ------------------------------------------
