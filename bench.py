@@ -137,6 +137,10 @@ def workload_and_scheme(args):
 # updates, two fast beta divisions); SER sweep 1 ~40, sweep 2 ~55 pair arithmetic.
 OPS_GAUSS = 180.0
 OPS_PER_PAIR = {"ssa": 95.0, "ssa_gauss": OPS_GAUSS, "sweep1": OPS_GAUSS + 40.0, "sweep2": OPS_GAUSS + 55.0}
+# the SSA by dependency levels (ssa_mode 2) draws each pair's Gaussian in its
+# execution kernel; its "ssa_gauss" phase is the level schedule, which has no
+# algorithmic operations of its own (it orders the pairs)
+OPS_PER_PAIR_LEVELS = {"ssa": 95.0 + OPS_GAUSS}
 KERNEL_OF_PHASE = {"ssa": "k_ssa_colour", "ssa_gauss": "k_ssa_gauss", "sweep1": "k_ser_sweep1",
                    "sweep2": "k_ser_sweep2", "force": "k_force_tile", "gather": "k_rank_gather",
                    "kick_drift": "k_kick_drift_key"}
@@ -145,7 +149,10 @@ KERNEL_OF_PHASE = {"ssa": "k_ssa_colour", "ssa_gauss": "k_ssa_gauss", "sweep1": 
 # named configuration with the caches kept warm
 # (profiles/launches_large_n4m_hybrid_mixed.md); reported only for that
 # configuration and kernel.
-MEASURED_TRAFFIC = {("large_n4m", "HYBRID", "mixed", "k_ssa_colour"): 168.6e6}
+MEASURED_TRAFFIC = {("large_n4m", "HYBRID", "mixed", "k_ssa_colour", 5): 168.6e6,
+                    # k_force_tile: 275.3 MB per launch on medium_n1m (tile edge 6, the same
+                    # kernel), scaled to 4M particles (traffic grows with the particle count)
+                    ("large_n4m", "HYBRID", "mixed", "k_force_tile", 6): 4.0 * 275.3e6}
 
 
 def pair_counts(w):
@@ -166,8 +173,8 @@ def pair_counts(w):
     return total, intra
 
 
-def algorithmic_model(w, phase: str, scheme: str, precision: str):
-    """Algorithmic work of the dominant phase in one step: unique pairs x lane
+def algorithmic_model(w, phase: str, scheme: str, precision: str, ssa_mode: int = 0):
+    """Algorithmic work of a phase in one step: unique pairs x lane
     operations per pair for the SSA and SER phases (ALU-bound), bytes for the
     memory-bound sort / force phases."""
     n = w.n_total
@@ -177,6 +184,8 @@ def algorithmic_model(w, phase: str, scheme: str, precision: str):
     pairs["ssa_gauss"] = pairs["ssa"]
     pairs["sweep2"] = pairs["sweep1"]
     state_bytes = 16 if precision == "mixed" else 32
+    if ssa_mode == 2 and phase in OPS_PER_PAIR_LEVELS:
+        return "alu", pairs[phase] * OPS_PER_PAIR_LEVELS[phase], "Gop/s"
     if phase in OPS_PER_PAIR:
         return "alu", pairs[phase] * OPS_PER_PAIR[phase], "Gop/s"
     if phase == "force":
@@ -265,27 +274,40 @@ def run_ours(args):
            "d2h_bytes_per_step": int(q.nbytes + p.nbytes + e.nbytes), "status": e2e_status}
 
     peaks, peak_src = measured_peaks()
-    bound, work, unit = algorithmic_model(w, dom, args.scheme, w.precision)
-    dom_s = phase_avg[dom] / 1e3
-    achieved = work / dom_s / 1e9
-    if bound == "alu":
-        clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = 152 * 128 * clk_mhz * 1e6 / 1e9   # FP32/INT32 lane-ops per second (G)
-        peak_note = f"152 SMs x 128 FP32/INT32 lanes x {clk_mhz:.0f} MHz ({peak_src} clock)"
-    else:
-        peak = float(peaks["hbm_gbs"])
-        peak_note = f"{peak_src} hbm_gbs"
-    kernel = KERNEL_OF_PHASE.get(dom, dom)
-    if dom == "ssa" and args.scheme == "HYBRID" and tuning.get("ssa_mode") == 1:
-        kernel = "k_ssa_domains"
-    if tuning.get("ssa_mode") == 2 and dom in ("ssa", "ssa_gauss"):
-        kernel = {"ssa": "k_ssa_exec", "ssa_gauss": "k_ssa_sched"}[dom]
-    traffic = MEASURED_TRAFFIC.get((w.name, args.scheme, w.precision, kernel))
-    if args.bricks:
-        traffic = None
-    roofline = {"bound": bound, "kernel": kernel, "phase": dom, "achieved": achieved, "peak": peak, "unit": unit,
+    mode = tuning.get("ssa_mode")
+
+    def phase_roofline(ph, secs=None):
+        bound, work, unit = algorithmic_model(w, ph, args.scheme, w.precision, mode)
+        t = (phase_avg[ph] / 1e3) if secs is None else secs
+        achieved = work / t / 1e9
+        if bound == "alu":
+            clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+            peak = 152 * 128 * clk_mhz * 1e6 / 1e9   # FP32/INT32 lane-ops per second (G)
+            peak_note = f"152 SMs x 128 FP32/INT32 lanes x {clk_mhz:.0f} MHz ({peak_src} clock)"
+        else:
+            peak = float(peaks["hbm_gbs"])
+            peak_note = f"{peak_src} hbm_gbs"
+        kernel = KERNEL_OF_PHASE.get(ph, ph)
+        if ph == "ssa" and args.scheme == "HYBRID" and mode == 1:
+            kernel = "k_ssa_domains"
+        if mode == 2 and ph in ("ssa", "ssa_gauss"):
+            kernel = {"ssa": "k_ssa_exec", "ssa_gauss": "k_ssa_sched"}[ph]
+        if mode == 3 and ph == "ssa":
+            kernel = "k_ssa_persistent"
+        traffic = None if args.bricks else MEASURED_TRAFFIC.get((w.name, args.scheme, w.precision, kernel,
+                                                                tuning.get("tile_edge")))
+        return {"bound": bound, "kernel": kernel, "phase": ph, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                 "peak_source": peak_note}
+
+    roofline = phase_roofline(dom)
+    roofline_phases = {ph: phase_roofline(ph) for ph in ("force", "ssa", "sweep1", "sweep2")
+                       if phase_avg.get(ph, 0) > 0}
+    if mode == 2 and args.scheme in ("HYBRID", "SSA"):
+        # the whole SSA part: the level schedule counted as overhead of the execution
+        r = phase_roofline("ssa", (phase_avg["ssa"] + phase_avg["ssa_gauss"]) / 1e3)
+        r.update({"kernel": "k_ssa_sched + k_ssa_exec", "phase": "ssa_gauss + ssa"})
+        roofline_phases["ssa_with_schedule"] = r
 
     drift = abs(obs1[0]["E"] - obs0[0]["E"]) / abs(obs0[0]["E"])
     out = {
@@ -304,6 +326,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": None,
         "roofline": roofline,
+        "roofline_phases": roofline_phases,
         "phase_ms": phase_avg,
         "energy_transient": {"rel_change_over_timed_steps": drift, "after_steps": 2 * args.warmup,
                              "status": status,
