@@ -213,8 +213,8 @@ def run_ours(args):
     # tune on a relaxed state: the first steps from the random start differ
     S.step(args.warmup, dt, args.scheme)
     tuning = S.autotune(args.scheme, dt, 10) if not args.no_autotune else S.tuning()
-    if args.ssa_mode is not None or args.ssa_group is not None:
-        S.set_tuning(ssa_mode=args.ssa_mode, ssa_group=args.ssa_group)
+    if args.ssa_mode is not None or args.ssa_group is not None or args.tile_edge is not None:
+        S.set_tuning(ssa_mode=args.ssa_mode, ssa_group=args.ssa_group, tile_edge=args.tile_edge)
         tuning = S.tuning()
     obs0 = S.observables()
 
@@ -724,9 +724,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--ssa-mode", type=int, choices=(0, 1), default=None,
+    ap.add_argument("--ssa-mode", type=int, choices=(0, 1, 2, 3), default=None,
                     help="force the SSA launch form: 0 one launch per colour class, 1 one launch over "
-                         "whole Hybrid domains")
+                         "whole Hybrid domains, 2 by dependency levels (schedule + execution), 3 the "
+                         "colour classes in one persistent launch")
+    ap.add_argument("--tile-edge", type=int, default=None, help="force the force pass's tile edge (cells)")
     ap.add_argument("--ssa-group", type=int, default=None, help="force the Hybrid domains per warp (1..8)")
     ap.add_argument("--fp64-steps", type=int, default=20,
                     help="steps of the FP64 GPU run of the same workload (0: skip)")
