@@ -84,7 +84,7 @@ struct dpde_handle {
     struct SsaCaps {
         // three tiers each: regular (one block per domain), deferred (a few
         // blocks per SM), large (one block per SM)
-        int scap_s[3] = {0, 0, 0}, ecap_s[3] = {0, 0, 0}, scap_x[3] = {0, 0, 0};
+        int scap_s[3] = {0, 0, 0}, ecap_s[3] = {0, 0, 0}, ccap_s[3] = {0, 0, 0}, scap_x[3] = {0, 0, 0};
         int grid_s[3] = {0, 0, 0}, grid_x[3] = {0, 0, 0};
         bool ok = false;   // domains small enough for the level form
     } ssa_caps[2];
@@ -251,9 +251,9 @@ void enqueue_ssa_levels(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, 
     cudaMemsetAsync(cnt, 0, 4 * sizeof(int), st);
     auto sched_tiers = [&]() {
         for (int t = 1; t < 3; ++t)
-            k_ssa_sched<T><<<K.grid_s[t], SCHED_THREADS, ssa_sched_smem(K.scap_s[t], K.ecap_s[t]), st>>>(
-                C, D, V, K.scap_s[t], K.ecap_s[t], 0, lst[t - 1], cnt + t - 1, t < 2 ? lst[t] : nullptr,
-                t < 2 ? cnt + t : nullptr);
+            k_ssa_sched<T><<<K.grid_s[t], SCHED_THREADS, ssa_sched_smem(K.scap_s[t], K.ecap_s[t], K.ccap_s[t]),
+                             st>>>(C, D, V, K.scap_s[t], K.ecap_s[t], K.ccap_s[t], 0, lst[t - 1], cnt + t - 1,
+                                   t < 2 ? lst[t] : nullptr, t < 2 ? cnt + t : nullptr);
     };
     auto exec_tiers = [&]() {
         for (int t = 1; t < 3; ++t)
@@ -262,8 +262,8 @@ void enqueue_ssa_levels(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, 
                 t < 2 ? cnt + 2 + t : nullptr, dt, sqrt_dt);
     };
     auto sched_regular = [&](cudaStream_t s, int d0, int n) {
-        k_ssa_sched<T><<<n, SCHED_THREADS, ssa_sched_smem(K.scap_s[0], K.ecap_s[0]), s>>>(
-            C, D, V, K.scap_s[0], K.ecap_s[0], d0, nullptr, nullptr, lst[0], cnt);
+        k_ssa_sched<T><<<n, SCHED_THREADS, ssa_sched_smem(K.scap_s[0], K.ecap_s[0], K.ccap_s[0]), s>>>(
+            C, D, V, K.scap_s[0], K.ecap_s[0], K.ccap_s[0], d0, nullptr, nullptr, lst[0], cnt);
     };
     auto exec_regular = [&](cudaStream_t s, int d0, int n) {
         k_ssa_exec<T><<<n, h->ssa_block, ssa_exec_smem<T>(K.scap_x[0]), s>>>(C, D, V, K.scap_x[0], d0, nullptr,
@@ -795,21 +795,26 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
             const double M = ndom > 0 ? (double)N / ndom : 0.0;
             auto up16 = [](double x) { return ((int)std::ceil(x) + 15) / 16 * 16; };
             // entries that fit beside sc particles in ~200 KB of schedule
-            auto ecap_fit = [&](int sc) {
+            auto ecap_fit = [&](int sc, int cc) {
                 return std::min(SSA_LOCAL_MAX,
-                                (int)((smem_big - SSA_LV_STRIDE * sizeof(int)) / 2 - (2 * sc + 1)) / 16 * 16);
+                                (int)((smem_big - (SSA_LV_STRIDE + cc) * sizeof(int)) / 2 - (2 * sc + 1)) / 16 * 16);
             };
             // schedule: 1.3 M particles / 1.2 M e entries; 2.5 M / 6.25 M e (a
             // brick compressed 2.5-fold holds ~6x the entries) in ~96 KB; the
-            // largest that ~200 KB hold
+            // largest that ~200 KB hold. Cell ranges staged for up to half as
+            // many cells as particles (density 3 has a third) in the first two.
             K.scap_s[0] = std::min(16384, up16(1.3 * M + 64));
-            K.ecap_s[0] = std::min(ecap_fit(K.scap_s[0]), up16(1.2 * M * e_pp + 256));
+            K.ccap_s[0] = K.scap_s[0] / 2;
+            K.ecap_s[0] = std::min(ecap_fit(K.scap_s[0], K.ccap_s[0]), up16(1.2 * M * e_pp + 256));
             K.scap_s[1] = std::min(16384, up16(2.5 * M + 64));
-            K.ecap_s[1] = std::min(ecap_fit(K.scap_s[1]), up16(6.25 * M * e_pp + 256));
-            while (K.ecap_s[1] > K.ecap_s[0] && ssa_sched_smem(K.scap_s[1], K.ecap_s[1]) > smem_big / 2)
+            K.ccap_s[1] = K.scap_s[1] / 2;
+            K.ecap_s[1] = std::min(ecap_fit(K.scap_s[1], K.ccap_s[1]), up16(6.25 * M * e_pp + 256));
+            while (K.ecap_s[1] > K.ecap_s[0] &&
+                   ssa_sched_smem(K.scap_s[1], K.ecap_s[1], K.ccap_s[1]) > smem_big / 2)
                 K.ecap_s[1] = std::max(K.ecap_s[0], K.ecap_s[1] * 7 / 8 / 16 * 16);
             K.scap_s[2] = 16384;
-            K.ecap_s[2] = ecap_fit(K.scap_s[2]);
+            K.ccap_s[2] = 0;
+            K.ecap_s[2] = ecap_fit(K.scap_s[2], 0);
             // execution: M + 5 sqrt(M) + 32 particles; 2.5 M in <= 96 KB; ~200 KB
             const int xfit = (int)((smem_big - 32) / per);
             K.scap_x[0] = std::min(xfit, ((int)std::ceil(M + 5.0 * std::sqrt(M) + 32) + 31) / 32 * 32);
@@ -817,7 +822,8 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
             K.scap_x[2] = xfit;
             const size_t smem_sm = 227 * 1024;
             K.grid_s[0] = ndom;
-            K.grid_s[1] = h->nsm * std::max<int>(1, (int)(smem_sm / (ssa_sched_smem(K.scap_s[1], K.ecap_s[1]) + 1024)));
+            K.grid_s[1] = h->nsm * std::max<int>(1, (int)(smem_sm / (ssa_sched_smem(K.scap_s[1], K.ecap_s[1],
+                                                                                      K.ccap_s[1]) + 1024)));
             K.grid_s[2] = h->nsm;
             K.grid_x[0] = ndom;
             const size_t xs1 = h->mixed ? ssa_exec_smem<float>(K.scap_x[1]) : ssa_exec_smem<double>(K.scap_x[1]);
@@ -944,7 +950,7 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
         size_t ms = 0, mx = 0;
         for (const auto& K : h->ssa_caps)
             for (int t = 0; t < 3; ++t) {
-                ms = std::max(ms, ssa_sched_smem(K.scap_s[t], K.ecap_s[t]));
+                ms = std::max(ms, ssa_sched_smem(K.scap_s[t], K.ecap_s[t], K.ccap_s[t]));
                 mx = std::max(mx, h->mixed ? ssa_exec_smem<float>(K.scap_x[t]) : ssa_exec_smem<double>(K.scap_x[t]));
             }
         const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;

@@ -685,12 +685,21 @@ __device__ __forceinline__ void force_tile_run(const Ctx<T>& C, int tile, const 
             const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
             const T ox = (T)(hx - cxh) * lx, oy = (T)(hy - cyh) * ly, oz = (T)(hz - czh) * lz;
             const int br = hbrick[h];
-            for (int k = 0; k < n; ++k) {
-                vec qv = C.qB[g + k];
-                qv.x += ox; qv.y += oy; qv.z += oz;
-                hq[b + k] = qv;
-                hglob[b + k] = g + k;
-                hbr[b + k] = br;
+            // four loads in flight at a time (a cell holds ~3 particles)
+            for (int k0 = 0; k0 < n; k0 += 4) {
+                vec qv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (k0 + u < n) qv[u] = C.qB[g + k0 + u];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (k0 + u < n) {
+                        const int k = k0 + u;
+                        qv[u].x += ox; qv[u].y += oy; qv[u].z += oz;
+                        hq[b + k] = qv[u];
+                        hglob[b + k] = g + k;
+                        hbr[b + k] = br;
+                    }
             }
         }
     }
@@ -769,27 +778,30 @@ __device__ __forceinline__ void force_tile_run(const Ctx<T>& C, int tile, const 
             const T ddx = qi.x - qj.x, ddy = qi.y - qj.y, ddz = qi.z - qj.z;
             return ddx * ddx + ddy * ddy + ddz * ddz < C.rc2 && j != hi;
         };
-        auto record = [&](int j) {
-            if (nh == HIT_BUF) flush();
-            myhits[nh * TILE_THREADS] = (unsigned short)j;
-            ++nh;
-        };
         for (int row = 0; row < 9; ++row) {
             const int base = hc + (row / 3 - 1) * HX * HY + (row % 3 - 1) * HX - 1;
             const int je = act ? hstart[base + 3] : 0;
             int j = act ? hstart[base] : 0;
-            // four independent candidates per pass, hits kept in order
+            // four independent candidates per pass; every candidate is
+            // written to the next free buffer slot and the slot kept only on
+            // a hit (no branch per hit), so hits stay in order
             for (; j + 4 <= je; j += 4) {
+                if (nh > HIT_BUF - 4) flush();
                 const bool h0 = near(j), h1 = near(j + 1), h2 = near(j + 2), h3 = near(j + 3);
-                if (h0 | h1 | h2 | h3) {
-                    if (h0) record(j);
-                    if (h1) record(j + 1);
-                    if (h2) record(j + 2);
-                    if (h3) record(j + 3);
-                }
+                myhits[nh * TILE_THREADS] = (unsigned short)j;
+                nh += h0;
+                myhits[nh * TILE_THREADS] = (unsigned short)(j + 1);
+                nh += h1;
+                myhits[nh * TILE_THREADS] = (unsigned short)(j + 2);
+                nh += h2;
+                myhits[nh * TILE_THREADS] = (unsigned short)(j + 3);
+                nh += h3;
             }
-            for (; j < je; ++j)
-                if (near(j)) record(j);
+            for (; j < je; ++j) {
+                if (nh == HIT_BUF) flush();
+                myhits[nh * TILE_THREADS] = (unsigned short)j;
+                nh += near(j);
+            }
         }
         flush();
         if (act) force_finish<T, LM>(C, i, half_dt, kick, o);

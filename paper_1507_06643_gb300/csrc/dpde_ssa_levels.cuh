@@ -69,11 +69,13 @@ struct SsaLevels {
     T* rec_w;
 };
 
-// shared bytes of k_ssa_sched for scap particles and ecap entries:
-// cnt (16-bit counters of levels 0..SSA_MAXLEV + 1, two to a word) |
+// shared bytes of k_ssa_sched for scap particles, ecap entries and ccap
+// cells: cnt (16-bit counters of levels 0..SSA_MAXLEV + 1, two to a word) |
+// cr[ccap] (the domain's cells in class order: local start | count << 16) |
 // rowoff[scap + 1] | L[scap] | ent[ecap] (16-bit)
-__host__ __device__ constexpr size_t ssa_sched_smem(int scap, int ecap) {
-    return (size_t)(SSA_LV_STRIDE / 2 + 1) * sizeof(int) + (((size_t)(2 * scap + 1 + ecap) * 2 + 15) / 16) * 16;
+__host__ __device__ constexpr size_t ssa_sched_smem(int scap, int ecap, int ccap) {
+    return (size_t)(SSA_LV_STRIDE / 2 + 1 + ccap) * sizeof(int) +
+           (((size_t)(2 * scap + 1 + ecap) * 2 + 15) / 16) * 16;
 }
 // shared bytes of k_ssa_exec for scap staged particles: p | eps | id, after
 // up to 31 bytes that align p to 32 bytes
@@ -150,16 +152,18 @@ __device__ __forceinline__ void ssa_rows_mmajor(int nb, const unsigned short* ro
 // when the domain exceeds scap particles, ecap entries or SSA_MAXLEV levels.
 template <class T>
 __device__ bool ssa_sched_domain(const Ctx<T>& C, const SsaDomains& D, const SsaLevels<T>& V, int d, int scap,
-                                 int ecap, unsigned char* smem) {
+                                 int ecap, int ccap, unsigned char* smem) {
     __shared__ int sh[32];
     __shared__ int s_flag, s_nlev;
+    __shared__ int s_off[NCOLOURS + 1];
     int sb, se;
     ssa_domain_range(C, D, d, sb, se);
     const int nb = se - sb;
     const int tid = threadIdx.x;
     if (nb > scap || nb > SSA_LOCAL_MAX) return false;
     int* cnt = reinterpret_cast<int*>(smem);
-    unsigned short* rowoff = reinterpret_cast<unsigned short*>(cnt + SSA_LV_STRIDE / 2 + 1);
+    unsigned int* cr = reinterpret_cast<unsigned int*>(cnt + SSA_LV_STRIDE / 2 + 1);
+    unsigned short* rowoff = reinterpret_cast<unsigned short*>(cr + ccap);
     unsigned short* L = rowoff + scap + 1;
     unsigned short* ent = L + scap;    // partner (local slot) of each entry, then its level
     if (tid == 0) {
@@ -167,7 +171,20 @@ __device__ bool ssa_sched_domain(const Ctx<T>& C, const SsaDomains& D, const Ssa
         s_nlev = 0;
     }
     for (int l = tid; l <= SSA_LV_STRIDE / 2; l += blockDim.x) cnt[l] = 0;
+    const int* off = D.off + (size_t)d * (NCOLOURS + 1);
+    for (int k = tid; k <= NCOLOURS; k += blockDim.x) s_off[k] = __ldg(off + k);
     __syncthreads();
+    // the domain's cells in class order, start and particle count, read once
+    // here rather than class by class in the walk (a domain with more cells
+    // than ccap reads them in the walk)
+    const int cbase = s_off[0], ncell = s_off[NCOLOURS] - cbase;
+    const bool cstaged = ncell <= ccap;
+    if (cstaged)
+        for (int u = tid; u < ncell; u += blockDim.x) {
+            const int c = __ldg(D.cells + cbase + u);
+            const int a = C.start[c], b = C.start[c + 1];
+            cr[u] = (unsigned int)(a - sb) | ((unsigned int)(b - a) << 16);
+        }
     // 1. row offsets of the domain's forward entries (16-bit: checked below)
     const int* fwd_n = C.fwd_n + sb;
     const int E = block_scan_runs(nb, rowoff, sh, [&](int i) { return fwd_n[i]; });
@@ -198,20 +215,25 @@ __device__ bool ssa_sched_domain(const Ctx<T>& C, const SsaDomains& D, const Ssa
     //    prefix maximum across the lanes,
     //      lev_j = j + 1 + max(L_s, max_{k <= j} (L[t_k] - k)),
     //    which is the recurrence lev_j = 1 + max(lev_{j-1}, L[t_j]) unrolled.
-    const int* off = D.off + (size_t)d * (NCOLOURS + 1);
     const int lane = tid & 31, sub = lane & 7, gbase = lane & ~7;
     const int group = tid >> 3, ngroups = blockDim.x >> 3;
     int mylev = 0;
     for (int k = 0; k < NCOLOURS; ++k) {
-        const int k0 = __ldg(off + k), k1 = __ldg(off + k + 1);
+        const int k0 = s_off[k], k1 = s_off[k + 1];
         if (k1 == k0) continue;   // uniform over the block
         for (int u0 = k0; u0 < k1; u0 += ngroups) {   // uniform over the block
             const int u = u0 + group;
             int s0 = 0, nrow = 0;
             if (u < k1) {
-                const int c = __ldg(D.cells + u);
-                s0 = C.start[c] - sb;
-                nrow = C.start[c + 1] - sb - s0;
+                if (cstaged) {
+                    const unsigned int v = cr[u - cbase];
+                    s0 = (int)(v & 0xffffu);
+                    nrow = (int)(v >> 16);
+                } else {
+                    const int c = __ldg(D.cells + u);
+                    s0 = C.start[c] - sb;
+                    nrow = C.start[c + 1] - sb - s0;
+                }
             }
             const int wrows = __reduce_max_sync(0xffffffffu, nrow);
             for (int r = 0; r < wrows; ++r) {
@@ -312,14 +334,15 @@ constexpr int SSA_PENDING = -2;
 
 template <class T>
 __global__ void __launch_bounds__(SCHED_THREADS, 8) k_ssa_sched(Ctx<T> C, SsaDomains D, SsaLevels<T> V, int scap,
-                                                                 int ecap, int d0, const int* __restrict__ list,
+                                                                 int ecap, int ccap, int d0,
+                                                                 const int* __restrict__ list,
                                                                  const int* __restrict__ nlist, int* defer,
                                                                  int* ndefer) {
     extern __shared__ __align__(16) unsigned char sched_smem[];
     const int n = list ? *nlist : (int)gridDim.x;
     for (int u = blockIdx.x; u < n; u += gridDim.x) {
         const int d = list ? list[u] : d0 + u;
-        if (!ssa_sched_domain(C, D, V, d, scap, ecap, sched_smem) && threadIdx.x == 0) {
+        if (!ssa_sched_domain(C, D, V, d, scap, ecap, ccap, sched_smem) && threadIdx.x == 0) {
             V.lv_n[d] = defer ? SSA_PENDING : -1;
             if (defer) defer[atomicAdd(ndefer, 1)] = d;
         }
