@@ -34,7 +34,8 @@ template <class T> struct Ctx {
                      //   [k * N + i], partner slots in SSA sequence order (segment, id)
     T* fwd_w;        //   w = 1 - r/r_cut of each entry
     vec* fwd_g;      // (G_it, w) of each entry, particle-major [i * nbr_cap + k] (the SSA
-                     //   chains' reading order), drawn before the SSA launches
+                     //   chains' reading order), drawn before the SSA launches; the level
+                     //   records of the SSA by levels; then the SER sweeps' delta p_ij
     int* fwd_n;
     const int* rep_of_slot;
     const int* rep_of_cell;
@@ -906,7 +907,10 @@ __device__ __forceinline__ T3<T> ser_dp(const Ctx<T>& C, int i, int k, uint32_t 
                  A * ((pi.z - pj.z) * C.inv_m) + Bn * G.z};
 }
 
-// first sweep: delta p_i = sum_j delta p_ij (Eq. SER_p)
+// first sweep: delta p_i = sum_j delta p_ij (Eq. SER_p). Each delta p_ij is
+// also written, entry-major like the list, into the forward-entry buffer
+// fwd_g (free once the SSA part of the step is done), so that the second
+// sweep reads it instead of drawing the pair's Gaussian again.
 template <class T>
 __global__ void k_ser_sweep1(Ctx<T> C, T dt, T sqrt_dt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -923,6 +927,10 @@ __global__ void k_ser_sweep1(Ctx<T> C, T dt, T sqrt_dt) {
         if (f < W.total) {
             const int io = base + o;
             d = ser_dp(C, io, k, step, dt, sdt, C.pB[io], C.idB[io], C.rep_of_slot[io]);
+            // kept for the second sweep, entry-major like the list
+            vec_t<T> dv;
+            dv.x = d.x; dv.y = d.y; dv.z = d.z; dv.w = T(0);
+            C.fwd_g[(size_t)k * C.N + io] = dv;
         } else {
             o = 32;
         }
@@ -992,7 +1000,7 @@ __global__ void k_ser_sweep2(Ctx<T> C, T dt, T sqrt_dt) {
             const vec_t<T> pi = C.pB[io];
             const vec_t<T> dpi = C.dp[io];
             const int j = C.nbr_j[(size_t)k * C.N + io];
-            const T3<T> d = ser_dp(C, io, k, step, dt, sdt, pi, C.idB[io], C.rep_of_slot[io]);
+            const vec_t<T> d = C.fwd_g[(size_t)k * C.N + io];   // delta p_ij of the first sweep
             const vec_t<T> pj = C.pB[j];
             const vec_t<T> dpj = C.dp[j];
             const T vix = pi.x * C.inv_m, viy = pi.y * C.inv_m, viz = pi.z * C.inv_m;
