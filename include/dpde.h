@@ -428,8 +428,8 @@ int dpde_set_tuning(dpde_handle* h, const dpde_tuning* t);
 
 /* Autotuner: times `steps` graph-replayed steps of `scheme` at `dt` (after
  * one untimed replay) for each candidate -- tile edges 4..8, then per-particle block sizes
- * 128, 256, 512, then SSA block sizes 32, 64, 128, then the SSA modes 2, 1
- * and 0, then (Hybrid in ssa_mode 1) 1..4 domains per warp, each stage keeping the
+ * 128, 256, 512, then SSA block sizes 32, 64, 128, then the SSA modes 2, 1,
+ * 0 and 3, then (Hybrid in ssa_mode 1) 1..4 domains per warp, each stage keeping the
  * best so far, a candidate replacing it only when more than 1% faster -- on
  * the handle's current state, restoring that state, its
  * forces and its step counter after every trial; then applies the fastest
@@ -443,8 +443,9 @@ int dpde_autotune(dpde_handle* h, int32_t scheme, double dt, int32_t steps, dpde
  * part has three schedule and three execution launches (ssa_mode 2: the
  * regular one and two for domains beyond its capacities), or one
  * launch drawing the Gaussians, then one per non-empty cell colour class
- * (ssa_mode 0, or DPDE_SSA in modes 1 and 2 without the level form) or one
- * for all domains (Hybrid in ssa_mode 1). No device work; the handle's state and step counter are
+ * (ssa_mode 0, or DPDE_SSA in modes 1 and 2 without the level form), one
+ * for all domains (Hybrid in ssa_mode 1) or one cooperative launch over all
+ * classes (ssa_mode 3). No device work; the handle's state and step counter are
  * unchanged. DPDE_ERR_ARG for a bad scheme. */
 int dpde_step_launches(dpde_handle* h, int32_t scheme, int64_t* launches);
 
