@@ -440,8 +440,10 @@ int dpde_autotune(dpde_handle* h, int32_t scheme, double dt, int32_t steps, dpde
 /* Number of kernel launches in one step of `scheme` (the kernel nodes of
  * the step's CUDA graph, captured here without being run; *launches, host
  * pointer). The count depends on the handle's geometry and tuning: the SSA
- * part has three schedule and three execution launches (ssa_mode 2: the
- * regular one and two for domains beyond its capacities), or one
+ * part has three schedule launches (ssa_mode 2: the regular one and two for
+ * domains beyond its capacities) and five execution launches (the regular
+ * one, two for the domains it defers, two for those the schedule deferred,
+ * the latter on a second stream beside the regular one), or one
  * launch drawing the Gaussians, then one per non-empty cell colour class
  * (ssa_mode 0, or DPDE_SSA in modes 1 and 2 without the level form), one
  * for all domains (Hybrid in ssa_mode 1) or one cooperative launch over all

@@ -51,6 +51,8 @@ struct dpde_handle {
     // overlapping the conversion kernels of the neighbouring chunks
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t xfer_ev[STATE_CHUNKS + 1] = {};
+    cudaStream_t ssa_stream = nullptr;       // the SSA schedule's deferred launches
+    cudaEvent_t ssa_ev[2] = {};
     // device buffers
     void *qA = nullptr, *pA = nullptr, *qB = nullptr, *pB = nullptr, *F = nullptr, *dp = nullptr;
     void* upot = nullptr;            // per-particle potential energy share (T)
@@ -233,7 +235,12 @@ void enqueue_force(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T half_dt, 
 // The SSA sequence by dependency levels (ssa_mode 2): the schedule of every
 // domain, then its execution; each kernel's regular launch (one block per
 // domain) defers domains beyond its shared-memory capacities to a second,
-// persistent launch with larger ones.
+// persistent launch with larger ones. The domains the schedule's regular
+// launch defers (the large ones of an uneven batch or a shock front) are
+// scheduled and then executed on a second stream, beside the execution's
+// regular launch, which leaves them alone: the two streams touch disjoint
+// domains, and the long chains of the large ones start before the many small
+// ones are done.
 template <class T>
 void enqueue_ssa_levels(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, T sqrt_dt, int whole) {
     const dpde_handle::SsaCaps& K = h->ssa_caps[whole];
@@ -244,22 +251,25 @@ void enqueue_ssa_levels(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, 
     V.lv_n = h->lv_n;
     V.rec_st = reinterpret_cast<uint32_t*>(h->fwd_g);
     V.rec_w = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(h->fwd_g) + ssa_rec_w_offset(h));
-    // counts: [0, 1] schedule tiers 1, 2; [2, 3] execution tiers 1, 2; then the lists
+    // counts: [0, 1] schedule tiers 1, 2; [2, 3] execution tiers 1, 2 of the
+    // domains the regular schedule kept; [4, 5] execution tiers 1, 2 of those
+    // it deferred; then the lists
     int* cnt = h->ssa_defer;
-    int* lst[4];
-    for (int k = 0; k < 4; ++k) lst[k] = cnt + 4 + (size_t)k * h->ndom_max;
-    cudaMemsetAsync(cnt, 0, 4 * sizeof(int), st);
-    auto sched_tiers = [&]() {
+    int* lst[SSA_NLISTS];
+    for (int k = 0; k < SSA_NLISTS; ++k) lst[k] = cnt + SSA_NLISTS + (size_t)k * h->ndom_max;
+    cudaMemsetAsync(cnt, 0, SSA_NLISTS * sizeof(int), st);
+    auto sched_tiers = [&](cudaStream_t s) {
         for (int t = 1; t < 3; ++t)
             k_ssa_sched<T><<<K.grid_s[t], SCHED_THREADS, ssa_sched_smem(K.scap_s[t], K.ecap_s[t], K.ccap_s[t]),
-                             st>>>(C, D, V, K.scap_s[t], K.ecap_s[t], K.ccap_s[t], 0, lst[t - 1], cnt + t - 1,
-                                   t < 2 ? lst[t] : nullptr, t < 2 ? cnt + t : nullptr);
+                             s>>>(C, D, V, K.scap_s[t], K.ecap_s[t], K.ccap_s[t], 0, lst[t - 1], cnt + t - 1,
+                                  t < 2 ? lst[t] : nullptr, t < 2 ? cnt + t : nullptr);
     };
-    auto exec_tiers = [&]() {
-        for (int t = 1; t < 3; ++t)
-            k_ssa_exec<T><<<K.grid_x[t], h->ssa_block, ssa_exec_smem<T>(K.scap_x[t]), st>>>(
-                C, D, V, K.scap_x[t], 0, lst[2 + t - 1], cnt + 2 + t - 1, t < 2 ? lst[2 + t] : nullptr,
-                t < 2 ? cnt + 2 + t : nullptr, dt, sqrt_dt);
+    // execution tiers 1, 2 over the list at index l0 (tier 1) and l0 + 1 (tier 2)
+    auto exec_tiers = [&](cudaStream_t s, int* first, int* nfirst, int l1) {
+        k_ssa_exec<T><<<K.grid_x[1], h->ssa_block, ssa_exec_smem<T>(K.scap_x[1]), s>>>(
+            C, D, V, K.scap_x[1], 0, first, nfirst, lst[l1], cnt + l1, dt, sqrt_dt);
+        k_ssa_exec<T><<<K.grid_x[2], h->ssa_block, ssa_exec_smem<T>(K.scap_x[2]), s>>>(
+            C, D, V, K.scap_x[2], 0, lst[l1], cnt + l1, nullptr, nullptr, dt, sqrt_dt);
     };
     auto sched_regular = [&](cudaStream_t s, int d0, int n) {
         k_ssa_sched<T><<<n, SCHED_THREADS, ssa_sched_smem(K.scap_s[0], K.ecap_s[0], K.ccap_s[0]), s>>>(
@@ -269,14 +279,27 @@ void enqueue_ssa_levels(dpde_handle* h, const Ctx<T>& C, cudaStream_t st, T dt, 
         k_ssa_exec<T><<<n, h->ssa_block, ssa_exec_smem<T>(K.scap_x[0]), s>>>(C, D, V, K.scap_x[0], d0, nullptr,
                                                                              nullptr, lst[2], cnt + 2, dt, sqrt_dt);
     };
-    phase(h, st, DPDE_PHASE_SSA_GAUSS, 0);
+    if (h->profiling) {   // phase by phase, one stream
+        phase(h, st, DPDE_PHASE_SSA_GAUSS, 0);
+        sched_regular(st, 0, D.n);
+        sched_tiers(st);
+        phase(h, st, DPDE_PHASE_SSA_GAUSS, 1);
+        phase(h, st, DPDE_PHASE_SSA, 0);
+        exec_regular(st, 0, D.n);
+        exec_tiers(st, lst[2], cnt + 2, 3);
+        exec_tiers(st, lst[0], cnt, 4);
+        phase(h, st, DPDE_PHASE_SSA, 1);
+        return;
+    }
     sched_regular(st, 0, D.n);
-    sched_tiers();
-    phase(h, st, DPDE_PHASE_SSA_GAUSS, 1);
-    phase(h, st, DPDE_PHASE_SSA, 0);
-    exec_regular(st, 0, D.n);
-    exec_tiers();
-    phase(h, st, DPDE_PHASE_SSA, 1);
+    cudaEventRecord(h->ssa_ev[0], st);
+    cudaStreamWaitEvent(h->ssa_stream, h->ssa_ev[0], 0);
+    sched_tiers(h->ssa_stream);                       // the deferred domains: scheduled,
+    exec_tiers(h->ssa_stream, lst[0], cnt, 4);        // then executed
+    exec_regular(st, 0, D.n);                         // the others, beside them
+    exec_tiers(st, lst[2], cnt + 2, 3);
+    cudaEventRecord(h->ssa_ev[1], h->ssa_stream);
+    cudaStreamWaitEvent(st, h->ssa_ev[1], 0);
 }
 
 template <class T>
@@ -499,6 +522,9 @@ void free_all(dpde_handle* h) {
         if (b) cudaFree(b);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->ssa_stream) cudaStreamDestroy(h->ssa_stream);
+    for (auto& ev : h->ssa_ev)
+        if (ev) cudaEventDestroy(ev);
     for (auto& ev : h->xfer_ev)
         if (ev) cudaEventDestroy(ev);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -853,6 +879,8 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     CKC(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     CKC(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
     for (auto& ev : h->xfer_ev) CKC(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CKC(cudaStreamCreateWithFlags(&h->ssa_stream, cudaStreamNonBlocking));
+    for (auto& ev : h->ssa_ev) CKC(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     const size_t n1 = (size_t)std::max(1, h->N), c1 = (size_t)std::max(1, h->ncells);
     const size_t tsz = h->mixed ? sizeof(float) : sizeof(double);
     CKC(cudaMalloc(&h->qA, vsz * n1));
@@ -945,7 +973,7 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
     h->ndom_max = std::max(1, std::max(h->nbricks, h->R));
     CKC(cudaMalloc(&h->lv_off, sizeof(int) * (size_t)h->ndom_max * SSA_LV_STRIDE));
     CKC(cudaMalloc(&h->lv_n, sizeof(int) * (size_t)h->ndom_max));
-    CKC(cudaMalloc(&h->ssa_defer, sizeof(int) * (4 + 4 * (size_t)h->ndom_max)));
+    CKC(cudaMalloc(&h->ssa_defer, sizeof(int) * (SSA_NLISTS + SSA_NLISTS * (size_t)h->ndom_max)));
     {
         size_t ms = 0, mx = 0;
         for (const auto& K : h->ssa_caps)

@@ -44,6 +44,7 @@ constexpr int SSA_LOAD_BATCH = 8;       // entries of a row taken together by th
 constexpr int SSA_COL_BATCH = 6;        // particles whose m-th entries a thread loads together
 constexpr int SSA_EXEC_THREADS_MAX = 128;
 constexpr int SSA_LOCAL_MAX = 65535;      // particles (and entries) of one domain: 16-bit local indices
+constexpr int SSA_NLISTS = 5;             // deferred-domain lists of one step (see enqueue_ssa_levels)
 
 // Domains of the SSA sequence: the cells of each domain sorted by colour
 // class (`cells`), the NCOLOURS + 1 class starts of every domain in `cells`
@@ -58,9 +59,13 @@ struct SsaDomains {
 
 // The level schedule of every domain: per domain the record offsets of its
 // levels (lv_off[d * SSA_LV_STRIDE + l], l = 0..nlev, records of level l in
-// [lv_off[l], lv_off[l + 1])), its level count (lv_n[d]; -1: no schedule,
-// executed along the colour order), and the records, domain d's at
-// [slot0(d) * cap, ...): (s_local | t_local << 16) and the weight w.
+// [lv_off[l], lv_off[l + 1])), its level count (lv_n[d]: nlev >= 0 from the
+// regular launch, -3 - nlev from a deferred one, -1 no schedule (executed
+// along the colour order), SSA_PENDING = -2 deferred and not yet scheduled),
+// and the records, domain d's at [slot0(d) * cap, ...): (s_local | t_local
+// << 16) and the weight w. The execution's regular launch, which may run
+// beside the schedule's deferred launches, takes only lv_n >= -1, so it never
+// reads a schedule that is still being written.
 template <class T>
 struct SsaLevels {
     int* lv_off;
@@ -152,7 +157,7 @@ __device__ __forceinline__ void ssa_rows_mmajor(int nb, const unsigned short* ro
 // when the domain exceeds scap particles, ecap entries or SSA_MAXLEV levels.
 template <class T>
 __device__ bool ssa_sched_domain(const Ctx<T>& C, const SsaDomains& D, const SsaLevels<T>& V, int d, int scap,
-                                 int ecap, int ccap, unsigned char* smem) {
+                                 int ecap, int ccap, bool deferred, unsigned char* smem) {
     __shared__ int sh[32];
     __shared__ int s_flag, s_nlev;
     __shared__ int s_off[NCOLOURS + 1];
@@ -321,9 +326,12 @@ __device__ bool ssa_sched_domain(const Ctx<T>& C, const SsaDomains& D, const Ssa
             V.rec_st[base + pos] = (uint32_t)i | ((uint32_t)min(max(x.t, 0), nb - 1) << 16);
             V.rec_w[base + pos] = x.w;
         });
-    if (tid == 0) V.lv_n[d] = nlev;
+    if (tid == 0) V.lv_n[d] = deferred ? -3 - nlev : nlev;
     return true;
 }
+
+// level count of a schedule stored as lv_n (see SsaLevels); -1 without one
+__device__ __forceinline__ int ssa_nlev(int v) { return v <= -3 ? -3 - v : v; }
 
 // One launch over the domains. Regular form (list == nullptr): block u takes
 // domain d0 + u. Deferred form: the blocks loop over `list`. A domain beyond
@@ -342,7 +350,7 @@ __global__ void __launch_bounds__(SCHED_THREADS, 8) k_ssa_sched(Ctx<T> C, SsaDom
     const int n = list ? *nlist : (int)gridDim.x;
     for (int u = blockIdx.x; u < n; u += gridDim.x) {
         const int d = list ? list[u] : d0 + u;
-        if (!ssa_sched_domain(C, D, V, d, scap, ecap, ccap, sched_smem) && threadIdx.x == 0) {
+        if (!ssa_sched_domain(C, D, V, d, scap, ecap, ccap, list != nullptr, sched_smem) && threadIdx.x == 0) {
             V.lv_n[d] = defer ? SSA_PENDING : -1;
             if (defer) defer[atomicAdd(ndefer, 1)] = d;
         }
@@ -364,7 +372,7 @@ __device__ __forceinline__ void ssa_exec_levels(const Ctx<T>& C, const SsaLevels
     const T amp0 = T(2) * C.sigma * sqrt_dt;   // amplitude of the map as gamma -> 0
     const T k2 = T(2) * dt * C.inv_m;
     const uint32_t step = (uint32_t)*C.step;
-    const int nlev = V.lv_n[d];
+    const int nlev = ssa_nlev(V.lv_n[d]);
     const int* lvo = V.lv_off + (size_t)d * SSA_LV_STRIDE;
     const size_t base = (size_t)sb * C.nbr_cap;
     const uint32_t* rst = V.rec_st + base;
@@ -470,21 +478,21 @@ __device__ void ssa_exec_classes(const Ctx<T>& C, const SsaDomains& D, int d, in
 }
 
 // One domain on the calling block: staged in shared memory when it fits in
-// scap slots, else deferred (regular form) or run on global memory (dense
-// form, defer == nullptr).
+// scap slots, else deferred (defer given) or run on global memory (defer ==
+// nullptr). The regular launch skips a domain whose schedule was deferred.
 template <class T>
 __device__ void ssa_exec_domain(const Ctx<T>& C, const SsaDomains& D, const SsaLevels<T>& V, int d, int scap,
-                                int* defer, int* ndefer, T dt, T sqrt_dt, unsigned char* smem) {
+                                bool regular, int* defer, int* ndefer, T dt, T sqrt_dt, unsigned char* smem) {
     int sb, se;
     ssa_domain_range(C, D, d, sb, se);
     const int nb = se - sb;
     if (nb == 0) return;
-    const int nlev = V.lv_n[d];
+    const int v = V.lv_n[d];
     const int rep = C.rep_of_cell[D.cell0[d]];
-    if (nlev == SSA_PENDING && defer) {   // its schedule comes from a later launch
-        if (threadIdx.x == 0) defer[atomicAdd(ndefer, 1)] = d;
-        return;
-    }
+    // deferred by the regular schedule: scheduled and executed by the deferred
+    // launches (perhaps running beside this one)
+    if (regular && v <= SSA_PENDING) return;
+    const int nlev = ssa_nlev(v);
     if (nlev < 0) {   // no schedule, even with the largest capacities: the colour order itself
         ssa_exec_classes(C, D, d, rep, dt, sqrt_dt);
         return;
@@ -513,10 +521,11 @@ __device__ void ssa_exec_domain(const Ctx<T>& C, const SsaDomains& D, const SsaL
     }
 }
 
-// Regular form (list == nullptr): block u takes domain d0 + u. Deferred
-// form: the blocks loop over `list`. A domain with more than scap particles,
-// or whose schedule is still pending, is passed on to `defer` when one is
-// given, else run on the state in global memory.
+// Regular form (list == nullptr): block u takes domain d0 + u, leaving out
+// the domains the regular schedule deferred (the deferred launches execute
+// them). Deferred form: the blocks loop over `list`. A domain with more than
+// scap particles is passed on to `defer` when one is given, else run on the
+// state in global memory.
 template <class T>
 __global__ void __launch_bounds__(SSA_EXEC_THREADS_MAX) k_ssa_exec(Ctx<T> C, SsaDomains D, SsaLevels<T> V,
                                                                     int scap, int d0, const int* __restrict__ list,
@@ -525,7 +534,8 @@ __global__ void __launch_bounds__(SSA_EXEC_THREADS_MAX) k_ssa_exec(Ctx<T> C, Ssa
     extern __shared__ __align__(16) unsigned char exec_smem[];
     const int n = list ? *nlist : (int)gridDim.x;
     for (int u = blockIdx.x; u < n; u += gridDim.x) {
-        ssa_exec_domain(C, D, V, list ? list[u] : d0 + u, scap, defer, ndefer, dt, sqrt_dt, exec_smem);
+        ssa_exec_domain(C, D, V, list ? list[u] : d0 + u, scap, list == nullptr, defer, ndefer, dt, sqrt_dt,
+                        exec_smem);
         __syncthreads();
     }
 }

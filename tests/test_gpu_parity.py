@@ -398,11 +398,13 @@ def test_ssa_launches_follow_colour_classes(box, bricks):
     S.set_tuning(ssa_mode=1)
     assert S.step_launches("HYBRID") - ser == 2
     assert S.step_launches("SSA") == ssa
-    # level form: three schedule and three execution launches (the regular one
-    # and two for deferred domains), for bricks and whole replicas
+    # level form: three schedule launches (the regular one and two for deferred
+    # domains) and five execution launches (the regular one, two for the
+    # domains it defers, two for those the schedule deferred), for bricks and
+    # whole replicas
     S.set_tuning(ssa_mode=2)
-    assert S.step_launches("HYBRID") - ser == 6
-    assert S.step_launches("SSA") - (ser - 1) == 6
+    assert S.step_launches("HYBRID") - ser == 8
+    assert S.step_launches("SSA") - (ser - 1) == 8
     # persistent form: the Gaussian pass and one cooperative launch over all classes
     S.set_tuning(ssa_mode=3)
     assert S.step_launches("HYBRID") - ser == 2
