@@ -136,6 +136,7 @@ def workload_and_scheme(args):
 # SSA pair map ~95 (one expm1, one rsqrt, momenta, dK, two compensated eps
 # updates, two fast beta divisions); SER sweep 1 ~40, sweep 2 ~55 pair arithmetic.
 OPS_GAUSS = 180.0
+OPS_FORCE = 20.0    # one pair force of the soft repulsion (one rsqrt, products, sums)
 OPS_PER_PAIR = {"ssa": 95.0, "ssa_gauss": OPS_GAUSS, "sweep1": OPS_GAUSS + 40.0, "sweep2": OPS_GAUSS + 55.0}
 # the SSA by dependency levels (ssa_mode 2) draws each pair's Gaussian in its
 # execution kernel; its "ssa_gauss" phase is the level schedule, which has no
@@ -193,6 +194,33 @@ def algorithmic_model(w, phase: str, scheme: str, precision: str, ssa_mode: int 
     if phase == "force":
         return "hbm", n * (state_bytes * 4.0), "GB/s"
     return "hbm", n * (state_bytes * 4.0 + 8 * 2 + 12), "GB/s"
+
+
+def step_roofline(w, scheme, ms_step, peaks, peak_src):
+    """The whole step against its modelled bound: the larger of the
+    algorithmic bytes (the mixed state read and written once, 68 B per
+    particle; 116 B in FP64) over the HBM peak and the algorithmic lane
+    operations (per unique pair one Gaussian triple, the force, and the SSA
+    map or the SER pair arithmetic of both sweeps) over the ALU peak."""
+    n = w.n_total
+    total, intra = pair_counts(w)
+    fd = OPS_PER_PAIR["ssa"] if scheme in ("HYBRID", "SSA") else 0.0
+    ser = OPS_PER_PAIR["sweep1"] - OPS_GAUSS + OPS_PER_PAIR["sweep2"] - OPS_GAUSS
+    if scheme == "HYBRID":
+        ops = total * (OPS_GAUSS + OPS_FORCE) + intra * fd + (total - intra) * ser
+    elif scheme == "SSA":
+        ops = total * (OPS_GAUSS + OPS_FORCE + fd)
+    else:
+        ops = total * (OPS_GAUSS + OPS_FORCE + ser)
+    nbytes = n * (68.0 if w.precision == "mixed" else 116.0)
+    clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu = 152 * 128 * clk_mhz * 1e6
+    hbm = float(peaks["hbm_gbs"]) * 1e9
+    model_s = max(nbytes / hbm, ops / alu)
+    return {"bound": "alu" if ops / alu >= nbytes / hbm else "hbm", "model_us": model_s * 1e6,
+            "measured_us": ms_step * 1e3, "frac": model_s / (ms_step / 1e3),
+            "ops_per_particle": ops / n, "bytes_per_particle": nbytes / n,
+            "peak_source": f"{peak_src} hbm_gbs; 152 SMs x 128 lanes x {clk_mhz:.0f} MHz"}
 
 
 def run_ours(args):
@@ -310,6 +338,7 @@ def run_ours(args):
         r = phase_roofline("ssa", (phase_avg["ssa"] + phase_avg["ssa_gauss"]) / 1e3)
         r.update({"kernel": "k_ssa_sched + k_ssa_exec", "phase": "ssa_gauss + ssa"})
         roofline_phases["ssa_with_schedule"] = r
+    roofline_step = step_roofline(w, args.scheme, ms / args.steps, peaks, peak_src)
 
     drift = abs(obs1[0]["E"] - obs0[0]["E"]) / abs(obs0[0]["E"])
     out = {
@@ -329,6 +358,7 @@ def run_ours(args):
         "gpu_launches": None,
         "roofline": roofline,
         "roofline_phases": roofline_phases,
+        "roofline_step": roofline_step,
         "phase_ms": phase_avg,
         "energy_transient": {"rel_change_over_timed_steps": drift, "after_steps": 2 * args.warmup,
                              "status": status,
