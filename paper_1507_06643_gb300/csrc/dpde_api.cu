@@ -4,6 +4,8 @@
 #include "dpde_ssa_levels.cuh"
 #include "dpde_ssa_persistent.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -16,6 +18,16 @@
 using namespace dpde;
 
 namespace {
+
+// A named NVTX range over the body of a C-ABI call (header-only NVTX v3: no
+// cost and no dependency unless a profiler is attached), so that profilers
+// can attribute work to the entry point that issued it.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 thread_local std::string g_create_error;
 
@@ -613,6 +625,7 @@ extern "C" {
 
 int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replica* replicas,
                 void* stream, dpde_handle** out) {
+    NvtxRange nvtx_range_("dpde_create");
     g_create_error.clear();
     if (!out) return fail(nullptr, DPDE_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -1020,6 +1033,7 @@ int dpde_create(const dpde_params* params, int32_t n_replicas, const dpde_replic
 
 int dpde_set_state(dpde_handle* h, const double* q, const double* p, const double* eps, int64_t step,
                    int32_t on_device) {
+    NvtxRange nvtx_range_("dpde_set_state");
     if (!h) return DPDE_ERR_ARG;
     if (h->N > 0 && (!q || !p || !eps)) return fail(h, DPDE_ERR_ARG, "q, p and eps are required");
     const size_t N = (size_t)h->N;
@@ -1037,6 +1051,7 @@ int dpde_set_state(dpde_handle* h, const double* q, const double* p, const doubl
 }
 
 int dpde_get_state(dpde_handle* h, double* q, double* p, double* eps, int32_t on_device) {
+    NvtxRange nvtx_range_("dpde_get_state");
     if (!h) return DPDE_ERR_ARG;
     const size_t N = (size_t)h->N;
     if (N > 0) {
@@ -1061,6 +1076,7 @@ int dpde_get_cells(dpde_handle* h, int32_t* cells) {
 }
 
 int dpde_step(dpde_handle* h, int64_t n, double dt, int32_t scheme, int32_t use_graph) {
+    NvtxRange nvtx_range_("dpde_step");
     if (!h) return DPDE_ERR_ARG;
     if (n < 0 || !(dt > 0) || !std::isfinite(dt) || scheme < DPDE_SER || scheme > DPDE_SSA)
         return fail(h, DPDE_ERR_ARG, "bad n, dt or scheme");
@@ -1167,6 +1183,7 @@ int dpde_set_tuning(dpde_handle* h, const dpde_tuning* t) {
 }
 
 int dpde_autotune(dpde_handle* h, int32_t scheme, double dt, int32_t steps, dpde_tuning* out) {
+    NvtxRange nvtx_range_("dpde_autotune");
     if (!h) return DPDE_ERR_ARG;
     if (scheme < DPDE_SER || scheme > DPDE_SSA || !(dt > 0) || !std::isfinite(dt) || steps < 1 || steps > 1000)
         return fail(h, DPDE_ERR_ARG, "bad scheme, dt or steps");
@@ -1298,6 +1315,7 @@ int dpde_step_launches(dpde_handle* h, int32_t scheme, int64_t* launches) {
 }
 
 int dpde_step_profiled(dpde_handle* h, int64_t n, double dt, int32_t scheme, double* phase_ms) {
+    NvtxRange nvtx_range_("dpde_step_profiled");
     if (!h || !phase_ms) return DPDE_ERR_ARG;
     if (n < 0 || !(dt > 0) || !std::isfinite(dt) || scheme < DPDE_SER || scheme > DPDE_SSA)
         return fail(h, DPDE_ERR_ARG, "bad n, dt or scheme");
@@ -1331,6 +1349,7 @@ int dpde_sync(dpde_handle* h) {
 }
 
 int dpde_observables(dpde_handle* h, dpde_obs* out) {
+    NvtxRange nvtx_range_("dpde_observables");
     if (!h || !out) return DPDE_ERR_ARG;
     if (h->mixed) enqueue_obs<float>(h, h->stream);
     else enqueue_obs<double>(h, h->stream);
@@ -1381,6 +1400,7 @@ uint64_t config_hash(const dpde_handle* h) {
 }  // namespace
 
 int dpde_checkpoint(dpde_handle* h, void* buf, uint64_t* size) {
+    NvtxRange nvtx_range_("dpde_checkpoint");
     if (!h || !size) return DPDE_ERR_ARG;
     const size_t N = (size_t)h->N;
     const size_t vsz = h->mixed ? sizeof(float4) : sizeof(d4);
@@ -1409,6 +1429,7 @@ int dpde_checkpoint(dpde_handle* h, void* buf, uint64_t* size) {
 }
 
 int dpde_restore(dpde_handle* h, const void* buf, uint64_t size) {
+    NvtxRange nvtx_range_("dpde_restore");
     if (!h || !buf || size < sizeof(CkptHeader)) return DPDE_ERR_ARG;
     CkptHeader hd;
     std::memcpy(&hd, buf, sizeof(hd));
