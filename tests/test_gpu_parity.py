@@ -636,6 +636,42 @@ def test_ssa_level_form_fallbacks_agree_bit_for_bit(precision, case):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ssa_two_streams_agree_with_one(precision):
+    """An uneven batch whose large domains the level form defers: a brick
+    grid of 500-particle domains, single-domain replicas of 3000 and 1500
+    particles (deferred by the regular schedule, so scheduled and executed on
+    the second stream beside the regular execution) and one of 1100 (kept by
+    the regular schedule, deferred by the regular execution). The graph
+    (two streams), eager launches (two streams) and the profiled step (one
+    stream, phase by phase) give the colour order's bits."""
+    from paper_1507_06643_gb300 import dpde
+    specs = [(4000, (cube(4000),) * 3, 50.0, 1.0, (2, 2, 2)), (3000, (cube(3000),) * 3, 50.0, 1.5, (1, 1, 1)),
+             (1500, (cube(1500),) * 3, 100.0, 0.7, (1, 1, 1)), (1100, (cube(1100),) * 3, 10.0, 1.2, (1, 1, 1))]
+    q, p, e = make_state(specs, 51, precision == "mixed")
+
+    def run(mode, how):
+        S = dpde.System(dpde.make_params(precision=precision),
+                        [dpde.make_replica(n, box, cv, br) for n, box, cv, _, br in specs])
+        S.set_tuning(ssa_mode=mode)
+        S.set_state(q, p, e)
+        if how == "graph":
+            S.step(3, 0.01, "HYBRID")
+        elif how == "eager":
+            S.step(3, 0.01, "HYBRID", use_graph=False)
+        else:
+            S.step_profiled(3, 0.01, "HYBRID")
+        assert S.sync() == dpde.DPDE_OK
+        out = S.get_state()
+        S.close()
+        return out
+
+    ref = run(0, "graph")
+    for how in ("graph", "eager", "profiled"):
+        for a, b in zip(ref, run(2, how)):
+            assert np.array_equal(a, b), how
+
+
 @pytest.mark.parametrize("edge", [2, 4, 5, 8])
 def test_tile_edge_changes_rounding_only(edge):
     ref = _run_tuned("fp64", None)
