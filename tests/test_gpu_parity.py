@@ -107,6 +107,52 @@ def test_parity_sizes(n, box, bricks, scheme, precision):
         break
 
 
+@pytest.mark.parametrize("scheme", ["SER", "HYBRID", "SEM", "SSA"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_parity_with_an_empty_replica(precision, scheme):
+    """A batch with an empty replica between two others: the empty one stays
+    empty and the others match the oracle, in every SSA form."""
+    from paper_1507_06643_gb300 import dpde
+    specs = [(500, (cube(500),) * 3, 50.0, 1.0, (2, 2, 2)), (0, (4.0, 4.0, 4.0), 50.0, 1.0, (1, 1, 1)),
+             (700, (cube(700),) * 3, 100.0, 1.5, (1, 1, 1))]
+    for _, (qg, pg, eg, obs), _ in assert_parity(specs, precision, scheme, 4, TOL[precision],
+                                                 seeds=range(71, 79)):
+        assert len(qg) == 1200 and obs[1]["K"] == 0.0 and obs[1]["U"] == 0.0
+        break
+    if scheme in ("HYBRID", "SSA"):
+        q, p, e = make_state(specs, 71, precision == "mixed")
+        outs = []
+        for mode in (0, 1, 2, 3):
+            S = dpde.System(dpde.make_params(precision=precision),
+                            [dpde.make_replica(n, box, cv, br) for n, box, cv, _, br in specs])
+            S.set_tuning(ssa_mode=mode)
+            S.set_state(q, p, e)
+            S.step(3, 0.01, scheme)
+            assert S.sync() == dpde.DPDE_OK
+            outs.append(S.get_state())
+            S.close()
+        for out in outs[1:]:
+            for a, b in zip(outs[0], out):
+                assert np.array_equal(a, b)
+
+
+def test_empty_system_steps_cleanly():
+    """A handle with no particles at all: every call succeeds and does nothing."""
+    from paper_1507_06643_gb300 import dpde
+    S = dpde.System(dpde.make_params(precision="mixed"), [dpde.make_replica(0, 4.0, 50.0, (1, 1, 1))])
+    z3, z1 = np.zeros((0, 3)), np.zeros(0)
+    S.set_state(z3, z3, z1)
+    S.step(3, 0.01, "HYBRID")
+    S.step(2, 0.01, "SER", use_graph=False)
+    assert S.sync() == dpde.DPDE_OK
+    q, p, e = S.get_state()
+    assert q.shape == (0, 3) and p.shape == (0, 3) and e.shape == (0,)
+    o = S.observables()[0]
+    assert o["K"] == 0.0 and o["U"] == 0.0 and o["Eint"] == 0.0
+    assert dpde.dpde_get_step(S.h) == 5
+    S.close()
+
+
 # ---- walls along z (the shock set-up's confining walls, Sec. V) ---------------------------
 
 @pytest.mark.parametrize("wall_u", [0.0, -1.5])
