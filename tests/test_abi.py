@@ -36,6 +36,8 @@ def test_invalid_arguments_are_rejected():
         (dpde.make_params(), [dpde.make_replica(100, 5.0, 100.0, (6, 1, 1))]),  # brick < r_cut
         (dpde.make_params(), [dpde.make_replica(100, 5.0, -1.0)]),
         (dpde.make_params(), [dpde.make_replica(-5, 5.0, 100.0)]),
+        (dpde.make_params(), [dpde.make_replica((1 << 27) + 1, 356.0, 100.0)]),   # particle limit
+        (dpde.make_params(), [dpde.make_replica(100, 1100.0, 100.0)]),            # cell limit 2^30
     ]:
         with pytest.raises(dpde.DPDEError) as ei:
             dpde.dpde_create(prm, reps)

@@ -640,7 +640,8 @@ def test_ssa_modes_agree_on_thin_and_batched_boxes(scheme):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("case", ["dense_brick", "denser_brick", "densest_brick", "global_state", "no_schedule"])
+@pytest.mark.parametrize("case", ["dense_brick", "denser_brick", "densest_brick", "global_state", "no_schedule",
+                                  "beyond_level_form"])
 def test_ssa_level_form_fallbacks_agree_bit_for_bit(precision, case):
     """The level form's paths beyond its regular shared-memory capacities give
     the colour order's bits: a brick holding more particles than the regular
@@ -649,7 +650,9 @@ def test_ssa_level_form_fallbacks_agree_bit_for_bit(precision, case):
     (both deferred to the largest tier); one domain too large for any
     staging (levels run on the state in global memory); one domain with more
     forward entries than a schedule holds (run class by class along the
-    colour order)."""
+    colour order); one domain above the 16,384 particles the level form
+    takes at all (ssa_mode 2 then runs the colour classes, launch for
+    launch)."""
     from paper_1507_06643_gb300 import dpde
     rng = np.random.default_rng(41)
     if case in ("dense_brick", "denser_brick", "densest_brick"):
@@ -666,10 +669,10 @@ def test_ssa_level_form_fallbacks_agree_bit_for_bit(precision, case):
             p = p.astype(np.float32).astype(np.float64)
         n = n0 + extra_n
     else:
-        n = 8000 if case == "global_state" else 15000
+        n = {"global_state": 8000, "no_schedule": 15000, "beyond_level_form": 20000}[case]
         L, bricks = cube(n), (1, 1, 1)
         q, p, e = make_state([(n, (L,) * 3, 50.0, 1.0, bricks)], 43, precision == "mixed")
-    outs = []
+    outs, launches = [], []
     for mode in (0, 2):
         S = dpde.System(dpde.make_params(precision=precision), [dpde.make_replica(n, (L,) * 3, 50.0, bricks)])
         S.set_tuning(ssa_mode=mode)
@@ -677,7 +680,10 @@ def test_ssa_level_form_fallbacks_agree_bit_for_bit(precision, case):
         S.step(3, 0.01, "HYBRID")
         assert S.sync() == dpde.DPDE_OK
         outs.append(S.get_state())
+        launches.append(S.step_launches("HYBRID"))
         S.close()
+    if case == "beyond_level_form":
+        assert launches[0] == launches[1]
     for a, b in zip(*outs):
         assert np.array_equal(a, b)
 
