@@ -151,11 +151,11 @@ KERNEL_OF_PHASE = {"ssa": "k_ssa_colour", "ssa_gauss": "k_ssa_gauss", "sweep1": 
 # (profiles/launches_large_n4m_hybrid_mixed.md); reported only for that
 # configuration and kernel.
 MEASURED_TRAFFIC = {("large_n4m", "HYBRID", "mixed", "k_ssa_colour", 5): 168.6e6,
-                    # k_force_tile: 284.7 MB per launch on medium_n1m at tile edge 5 and
-                    # 275.6 MB at edge 6, scaled to 4M particles (traffic grows with the
+                    # k_force_tile: 286.7 MB per launch on medium_n1m at tile edge 5 and
+                    # 276.8 MB at edge 6, scaled to 4M particles (traffic grows with the
                     # particle count)
-                    ("large_n4m", "HYBRID", "mixed", "k_force_tile", 5): 4.0 * 284.7e6,
-                    ("large_n4m", "HYBRID", "mixed", "k_force_tile", 6): 4.0 * 275.6e6}
+                    ("large_n4m", "HYBRID", "mixed", "k_force_tile", 5): 4.0 * 286.7e6,
+                    ("large_n4m", "HYBRID", "mixed", "k_force_tile", 6): 4.0 * 276.8e6}
 
 
 def pair_counts(w):

@@ -590,17 +590,18 @@ __device__ void force_one_global(const Ctx<T>& C, int i, T half_dt, int kick) {
 constexpr int TILE_THREADS = 256;
 constexpr int TILE_EDGE = 6;       // default tile edge (cells); the autotuner picks 4..8
 constexpr int TILE_EDGE_MAX = 8;
-constexpr int HIT_BUF = 32;        // hits buffered per thread (flushed when full)
+constexpr int HIT_BUF = 28;        // hits buffered per thread (flushed when full)
 
 // shared bytes before the staged particles, for halo cell capacity hcc
 // ((edge + 2)^3): hstart, gstart, hbrick, rowoff (edge^2 + 1 <= 65), nown, hits
 __host__ __device__ constexpr size_t tile_head_bytes(int hcc) {
     return ((size_t)(3 * hcc + 1 + 66) * sizeof(int) + (size_t)HIT_BUF * TILE_THREADS * 2 + 31) & ~(size_t)31;
 }
-// shared bytes per staged halo particle: position, global slot, brick, own index
+// shared bytes per staged halo particle: position, global slot, brick, own
+// index with its halo cell
 template <class T>
 __host__ __device__ constexpr size_t tile_per_particle() {
-    return sizeof(vec_t<T>) + 2 * sizeof(int) + sizeof(unsigned short);
+    return sizeof(vec_t<T>) + 2 * sizeof(int) + sizeof(unsigned int);
 }
 
 // One tile on the calling block. A tile whose halo holds more than hcap
@@ -621,7 +622,7 @@ __device__ __forceinline__ void force_tile_run(const Ctx<T>& C, int tile, const 
     const int nx = R.nc[0], ny = R.nc[1], nz = R.nc[2];
     // shared layout (sized for HC <= hcc = (edge + 2)^3):
     //   hstart[hcc+1] gstart[hcc] hbrick[hcc] rowoff[65] nown | hits[HIT_BUF][TILE_THREADS] (u16) |
-    //   q[hcap] glob[hcap] brick[hcap] own[hcap]
+    //   q[hcap] glob[hcap] brick[hcap] own[hcap] (u32: halo index | halo cell << 16)
     int* hstart = (int*)smem;
     int* gstart = hstart + hcc + 1;
     int* hbrick = gstart + hcc;
@@ -631,25 +632,42 @@ __device__ __forceinline__ void force_tile_run(const Ctx<T>& C, int tile, const 
     vec* hq = (vec*)(smem + tile_head_bytes(hcc));
     int* hglob = (int*)(hq + hcap);
     int* hbr = hglob + hcap;
-    unsigned short* own = (unsigned short*)(hbr + hcap);
+    unsigned int* own = (unsigned int*)(hbr + hcap);   // halo index | halo cell << 16
     const int* bt = brick_tab(C.tab, R);
-    // 1. halo cells: global start, count, brick
-    for (int h = threadIdx.x; h < HC; h += blockDim.x) {
-        const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
-        int x = org.y + hx - 1, y = org.z + hy - 1, z = org.w + hz - 1;
-        if (R.walls && (z < 0 || z >= nz)) {   // beyond a wall: an empty halo cell
-            gstart[h] = 0;
-            hstart[h] = 0;
-            hbrick[h] = -1;
-            continue;
+    // 1. halo cells: global start, count, brick (two cells per thread at a
+    //    time, their loads issued together)
+    for (int h0 = threadIdx.x; h0 < HC; h0 += 2 * blockDim.x) {
+        int xs[2], ys[2], zs[2], cs[2];
+        bool use[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int h = h0 + u * (int)blockDim.x;
+            const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+            int x = org.y + hx - 1, y = org.z + hy - 1, z = org.w + hz - 1;
+            use[u] = h < HC && !(R.walls && (z < 0 || z >= nz));   // beyond a wall: an empty halo cell
+            x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+            y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+            z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+            xs[u] = x; ys[u] = y; zs[u] = z;
+            cs[u] = use[u] ? cell_index(C.tab, R, x, y, z) : 0;
         }
-        x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
-        y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-        z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
-        const int c = cell_index(C.tab, R, x, y, z);
-        gstart[h] = C.start[c];
-        hstart[h] = C.start[c + 1] - C.start[c];
-        hbrick[h] = __ldg(bt + x) | (__ldg(bt + nx + y) << 10) | (__ldg(bt + nx + ny + z) << 20);
+        int a[2] = {0, 0}, b[2] = {0, 0}, br[2] = {-1, -1};
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (use[u]) {
+                a[u] = C.start[cs[u]];
+                b[u] = C.start[cs[u] + 1];
+                br[u] = __ldg(bt + xs[u]) | (__ldg(bt + nx + ys[u]) << 10) | (__ldg(bt + nx + ny + zs[u]) << 20);
+            }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int h = h0 + u * (int)blockDim.x;
+            if (h < HC) {
+                gstart[h] = a[u];
+                hstart[h] = b[u] - a[u];
+                hbrick[h] = br[u];
+            }
+        }
     }
     __syncthreads();
     // 2. exclusive scan of the halo counts (a run of up to 4 per thread, HC <= 1000)
@@ -704,16 +722,31 @@ __device__ __forceinline__ void force_tile_run(const Ctx<T>& C, int tile, const 
             }
         }
     }
-    const int nrow = dim.y * dim.z;
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int r = 0; r < nrow; ++r) {
-            rowoff[r] = acc;
+    const int nrow = dim.y * dim.z;   // <= 64: a row per thread of the first two warps
+    {
+        __shared__ int s_w0;
+        const int r = threadIdx.x;
+        int v = 0;
+        if (r < nrow) {
             const int h = ((r / dim.y + 1) * HY + (r % dim.y + 1)) * HX;
-            acc += hstart[h + dim.x + 1] - hstart[h + 1];
+            v = hstart[h + dim.x + 1] - hstart[h + 1];
         }
-        rowoff[nrow] = acc;
-        *nown = acc;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((r & 31) >= o) x += y;
+        }
+        if (r == 31) s_w0 = x;
+        __syncthreads();
+        if (r < nrow) {
+            const int incl = x + (r >= 32 ? s_w0 : 0);
+            rowoff[r] = incl - v;
+            if (r == nrow - 1) {
+                rowoff[nrow] = incl;
+                *nown = incl;
+            }
+        }
     }
     __syncthreads();
     if (!staged) {
@@ -731,10 +764,13 @@ __device__ __forceinline__ void force_tile_run(const Ctx<T>& C, int tile, const 
         }
         return;
     }
-    for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
+    // own particles in row order, a thread per own cell
+    for (int rc = threadIdx.x; rc < nrow * dim.x; rc += blockDim.x) {
+        const int r = rc / dim.x, cx = rc - r * dim.x;
         const int h = ((r / dim.y + 1) * HY + (r % dim.y + 1)) * HX;
-        const int b = hstart[h + 1], e = hstart[h + dim.x + 1];
-        for (int k = b; k < e; ++k) own[rowoff[r] + (k - b)] = (unsigned short)k;
+        const int b = hstart[h + 1], k1 = hstart[h + cx + 2];
+        const unsigned int cell = (unsigned int)(h + cx + 1) << 16;
+        for (int k = hstart[h + cx + 1]; k < k1; ++k) own[rowoff[r] + (k - b)] = (unsigned int)k | cell;
     }
     __syncthreads();
     // 5. each own particle: rows in step, hits recorded, then processed
@@ -743,25 +779,13 @@ __device__ __forceinline__ void force_tile_run(const Ctx<T>& C, int tile, const 
     for (int k0 = 0; k0 < no; k0 += blockDim.x) {
         const int k = k0 + threadIdx.x;
         const bool act = k < no;
-        const int hi = act ? own[k] : 0;
+        const unsigned int ow = act ? own[k] : 0u;
+        const int hi = (int)(ow & 0xffffu);
         const vec qi = hq[hi];
         const int i = hglob[hi];
         const int mybrick = hbr[hi];
         // halo coordinates of i's cell, from its row base
-        int hc = 0;
-        {
-            // the own cell is found from the own-row table
-            int lo = 0, hi2 = nrow;   // row r: rowoff[r] <= k < rowoff[r + 1]
-            while (hi2 - lo > 1) {
-                const int mid = (lo + hi2) >> 1;
-                if (rowoff[mid] <= k) lo = mid;
-                else hi2 = mid;
-            }
-            const int h = ((lo / dim.y + 1) * HY + (lo % dim.y + 1)) * HX;
-            int cx = 1;
-            while (cx < dim.x && hstart[h + cx + 1] <= hi) ++cx;
-            hc = h + cx;
-        }
+        const int hc = (int)(ow >> 16);
         PairOut<T> o;
         int nh = 0;
         auto flush = [&]() {
