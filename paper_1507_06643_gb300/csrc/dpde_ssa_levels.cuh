@@ -508,10 +508,29 @@ __device__ void ssa_exec_domain(const Ctx<T>& C, const SsaDomains& D, const SsaL
     vec_t<T>* P = reinterpret_cast<vec_t<T>*>(((size_t)smem + 31) & ~(size_t)31);
     eps_t<T>* Es = reinterpret_cast<eps_t<T>*>(P + scap);
     uint32_t* ID = reinterpret_cast<uint32_t*>(Es + scap);
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        P[i] = C.pB[sb + i];
-        Es[i] = C.eB[sb + i];
-        ID[i] = C.idB[sb + i];
+    // four particles per thread in flight
+    for (int i0 = threadIdx.x; i0 < nb; i0 += 4 * blockDim.x) {
+        vec_t<T> pv[4];
+        eps_t<T> ev[4];
+        uint32_t iv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * (int)blockDim.x;
+            if (i < nb) {
+                pv[u] = C.pB[sb + i];
+                ev[u] = C.eB[sb + i];
+                iv[u] = C.idB[sb + i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * (int)blockDim.x;
+            if (i < nb) {
+                P[i] = pv[u];
+                Es[i] = ev[u];
+                ID[i] = iv[u];
+            }
+        }
     }
     __syncthreads();
     ssa_exec_levels(C, V, d, sb, rep, P, Es, ID, dt, sqrt_dt);
