@@ -784,7 +784,7 @@ __device__ __forceinline__ void force_tile_run(const Ctx<T>& C, int tile, const 
         const vec qi = hq[hi];
         const int i = hglob[hi];
         const int mybrick = hbr[hi];
-        // halo coordinates of i's cell, from its row base
+        // i's halo cell, stored beside its halo index
         const int hc = (int)(ow >> 16);
         PairOut<T> o;
         int nh = 0;
